@@ -1,0 +1,134 @@
+"""ctypes wrapper of the CPU oracle (oracle.c).
+
+TEST INFRASTRUCTURE ONLY: the test suite, the smoke check and the
+CPU-baseline leg of the benchmark use it.  The GPU library never imports it.
+"""
+
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "oracle.c")
+_LIB_PATH = os.path.join(_HERE, "liboracle.so")
+_lib = None
+
+ERRORS = {
+    0: "ok",
+    -1: "invalid arguments",
+    -2: "too many sets",
+    -3: "not synchronizing",
+    -4: "word does not fit",
+    -5: "out of host memory",
+    -6: "no reset word up to max_len",
+}
+
+
+class OracleError(RuntimeError):
+    def __init__(self, code: int, where: str):
+        super().__init__(f"{where}: {ERRORS.get(code, code)}")
+        self.code = code
+
+
+def build(force: bool = False) -> str:
+    """Compile liboracle.so with gcc (plain -O2, portable: no -march)."""
+    if force or not os.path.exists(_LIB_PATH) or os.path.getmtime(_LIB_PATH) < os.path.getmtime(_SRC):
+        tmp = _LIB_PATH + f".tmp{os.getpid()}"
+        subprocess.check_call(["gcc", "-O2", "-std=c11", "-shared", "-fPIC", "-o", tmp, _SRC])
+        os.replace(tmp, _LIB_PATH)
+    return _LIB_PATH
+
+
+def _load():
+    global _lib
+    if _lib is None:
+        build()
+        lib = ctypes.CDLL(_LIB_PATH)
+        i32, i64, p = ctypes.c_int32, ctypes.c_int64, ctypes.c_void_p
+        lib.oracle_brute.argtypes = [ctypes.c_int, ctypes.c_int, p, ctypes.c_int, p, p]
+        lib.oracle_forward.argtypes = [ctypes.c_int, ctypes.c_int, p, i64, p, p, i32, p, i32, p]
+        lib.oracle_level_sizes.argtypes = [ctypes.c_int, ctypes.c_int, p, ctypes.c_int, i32, i64, p]
+        lib.oracle_bidir.argtypes = [ctypes.c_int, ctypes.c_int, p, i64, p, p, i32, p, p, p, p, i32]
+        lib.oracle_is_synchronizing.argtypes = [ctypes.c_int, ctypes.c_int, p]
+        for f in (lib.oracle_brute, lib.oracle_forward, lib.oracle_level_sizes, lib.oracle_bidir,
+                  lib.oracle_is_synchronizing):
+            f.restype = ctypes.c_int
+        _lib = lib
+    return _lib
+
+
+def _delta(delta):
+    d = np.ascontiguousarray(np.asarray(delta, dtype=np.int32))
+    if d.ndim != 2:
+        raise ValueError("delta must be [k][n]")
+    return d, d.shape[1], d.shape[0]
+
+
+def _ptr(a):
+    return a.ctypes.data_as(ctypes.c_void_p)
+
+
+def brute(delta, max_len: int = 24):
+    """O0: (r, word) by enumerating words in length-lexicographic order."""
+    d, n, k = _delta(delta)
+    r = np.zeros(1, np.int32)
+    w = np.zeros(64, np.uint8)
+    rc = _load().oracle_brute(n, k, _ptr(d), max_len, _ptr(r), _ptr(w))
+    if rc:
+        raise OracleError(rc, "oracle_brute")
+    return int(r[0]), w[: r[0]].tolist()
+
+
+def forward(delta, max_sets: int = 50_000_000, word_cap: int = 1 << 20):
+    """O1: (r, word, level_sizes) by forward BFS over the power automaton."""
+    d, n, k = _delta(delta)
+    r = np.zeros(1, np.int32)
+    w = np.zeros(word_cap, np.uint8)
+    sizes = np.zeros(word_cap + 1, np.int64)
+    nl = np.zeros(1, np.int32)
+    rc = _load().oracle_forward(n, k, _ptr(d), max_sets, _ptr(r), _ptr(w), word_cap, _ptr(sizes),
+                                len(sizes), _ptr(nl))
+    if rc:
+        raise OracleError(rc, "oracle_forward")
+    return int(r[0]), w[: r[0]].tolist(), sizes[: nl[0]].tolist()
+
+
+def level_sizes(delta, direction: int, depth: int, max_sets: int = 50_000_000):
+    """Sizes of deduplicated levels 0..depth: direction 0 = images of Q,
+    1 = preimages of singletons."""
+    d, n, k = _delta(delta)
+    sizes = np.zeros(depth + 1, np.int64)
+    rc = _load().oracle_level_sizes(n, k, _ptr(d), direction, depth, max_sets, _ptr(sizes))
+    if rc:
+        raise OracleError(rc, "oracle_level_sizes")
+    return sizes.tolist()
+
+
+def bidir(delta, max_sets: int = 50_000_000, word_cap: int = 1 << 20):
+    """O2: (r, word, fwd_sizes, bwd_sizes) by bidirectional BFS (Alg. 1,
+    duplicate deletion and equality history only)."""
+    d, n, k = _delta(delta)
+    r = np.zeros(1, np.int32)
+    w = np.zeros(word_cap, np.uint8)
+    cap = 4096
+    fs = np.zeros(cap, np.int64)
+    bs = np.zeros(cap, np.int64)
+    nf = np.zeros(1, np.int32)
+    nb = np.zeros(1, np.int32)
+    rc = _load().oracle_bidir(n, k, _ptr(d), max_sets, _ptr(r), _ptr(w), word_cap, _ptr(fs), _ptr(nf),
+                              _ptr(bs), _ptr(nb), cap)
+    if rc:
+        raise OracleError(rc, "oracle_bidir")
+    return int(r[0]), w[: r[0]].tolist(), fs[: nf[0]].tolist(), bs[: nb[0]].tolist()
+
+
+def is_synchronizing(delta) -> bool:
+    d, n, k = _delta(delta)
+    rc = _load().oracle_is_synchronizing(n, k, _ptr(d))
+    if rc < 0:
+        raise OracleError(rc, "oracle_is_synchronizing")
+    return bool(rc)

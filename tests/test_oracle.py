@@ -1,0 +1,218 @@
+"""Pins of the CPU oracle against facts fixed by the paper and by mathematics.
+
+None of these checks reuses the oracle's own code: hand derivations
+(tests/golden/hand_examples.json), the closed form for Cerny automata
+(Section 1.1), the definition of a reset word (Section 1) applied directly
+with numpy, brute-force enumeration of words in plain Python, exhaustive
+enumeration of all small binary automata, and bounds (Frankl-Pin, Section
+1.1; sink automata, Section 3.1.1).
+"""
+
+import itertools
+import json
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2207_05495_gb300 import gen
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def resets(delta, word):
+    """|delta(Q, w)| == 1, straight from the definition (Section 1)."""
+    delta = np.asarray(delta)
+    states = np.arange(delta.shape[1])
+    for a in word:
+        states = delta[a][states]
+    return len(np.unique(states)) == 1
+
+
+def brute_levels(delta, direction, depth):
+    """Deduplicated level sizes by enumerating every word (plain Python).
+
+    Forward: D_i = {delta(Q, w) : |w| = i}; level i = D_i minus every
+    D_i' with i' < i.  Backward: E_j = nonempty {delta^{-1}({q}, y) : |y| = j};
+    level j = E_j minus every earlier E_j'."""
+    delta = [list(map(int, row)) for row in np.asarray(delta)]
+    k, n = len(delta), len(delta[0])
+    seen, sizes = set(), []
+    for d in range(depth + 1):
+        cur = set()
+        for w in itertools.product(range(k), repeat=d):
+            if direction == 0:
+                s = set(range(n))
+                for a in w:
+                    s = {delta[a][q] for q in s}
+                cur.add(frozenset(s))
+            else:
+                for q in range(n):
+                    s = {q}
+                    for a in reversed(w):  # delta^{-1}({q}, w) = pre(...pre({q}, w_last)...)
+                        s = {p for p in range(n) if delta[a][p] in s}
+                    if s:
+                        cur.add(frozenset(s))
+        new = cur - seen
+        sizes.append(len(new))
+        seen |= cur
+    return sizes
+
+
+def cerny_word(n):
+    """b (a^{n-1} b)^{n-2}: each a^{n-1} b removes one state of {1..m}."""
+    return [] if n == 1 else [1] + ([0] * (n - 1) + [1]) * (n - 2)
+
+
+# ---------------------------------------------------------------- hand examples
+
+with open(os.path.join(GOLDEN, "hand_examples.json")) as fh:
+    HAND = json.load(fh)["examples"]
+
+
+@pytest.mark.parametrize("ex", HAND, ids=[e["name"] for e in HAND])
+def test_hand_examples(ex):
+    d = np.array(ex["delta"], dtype=np.int32)
+    r, w, fs = oracle.forward(d)
+    assert r == ex["r"] and w == ex["word"]
+    assert fs == ex["fwd_sizes"]
+    assert oracle.level_sizes(d, 1, len(ex["bwd_sizes"]) - 1) == ex["bwd_sizes"]
+    rb, wb, fsb, bsb = oracle.bidir(d)
+    assert (rb, wb) == (ex["r"], ex["word"])
+    assert fsb == ex["fwd_sizes"][: len(fsb)]
+    assert bsb == ex["bwd_sizes"][: len(bsb)]
+    assert oracle.brute(d, 8) == (ex["r"], ex["word"])
+
+
+# ---------------------------------------------------------------- Cerny closed form
+
+@pytest.mark.parametrize("n", range(1, 17))
+def test_cerny_forward_closed_form(n):
+    d = gen.cerny(n)
+    r, w, _ = oracle.forward(d)
+    assert r == (n - 1) ** 2
+    assert w == cerny_word(n)
+    assert resets(d, w)
+
+
+@pytest.mark.parametrize("n", range(1, 6))
+def test_cerny_brute_unique_word(n):
+    # brute force returns the least word; the closed-form word is the least
+    d = gen.cerny(n)
+    assert oracle.brute(d, (n - 1) ** 2) == ((n - 1) ** 2, cerny_word(n))
+
+
+@pytest.mark.parametrize("n", [2, 3, 5, 8, 12, 16, 20])
+def test_cerny_bidirectional(n):
+    d = gen.cerny(n)
+    r, w, _, _ = oracle.bidir(d)
+    assert r == (n - 1) ** 2 and w == cerny_word(n)
+
+
+# ---------------------------------------------------------------- brute force
+
+def _small_random(count, n_range, k_range, seed0):
+    out = []
+    for i in range(count):
+        rng = np.random.default_rng(seed0 + i)
+        n = int(rng.integers(n_range[0], n_range[1] + 1))
+        k = int(rng.integers(k_range[0], k_range[1] + 1))
+        out.append(gen.random_automaton(n, k, seed0 * 1000 + i))
+    return out
+
+
+@pytest.mark.parametrize("d", _small_random(40, (2, 7), (1, 3), 11))
+def test_forward_equals_brute(d):
+    rb, wb = oracle.brute(d, 16)
+    r, w, _ = oracle.forward(d)
+    assert (r, w) == (rb, wb)
+    assert resets(d, w)
+
+
+@pytest.mark.parametrize("d", _small_random(12, (2, 5), (1, 3), 23))
+def test_level_sizes_equal_word_enumeration(d):
+    depth = 5
+    for direction in (0, 1):
+        assert oracle.level_sizes(d, direction, depth) == brute_levels(d, direction, depth)
+
+
+def test_all_binary_automata_n2_n3():
+    """Every binary automaton on 2 and 3 states: the oracle's forward BFS,
+    brute force and pair check agree with the input filter, and on 2
+    states exactly the 12 automata with a constant letter synchronize, each
+    with r = 1."""
+    for n in (2, 3):
+        count = 0
+        for flat in itertools.product(range(n), repeat=2 * n):
+            d = np.array(flat, dtype=np.int32).reshape(2, n)
+            sync = gen.is_synchronizing(d)
+            assert oracle.is_synchronizing(d) == sync
+            if not sync:
+                with pytest.raises(oracle.OracleError):
+                    oracle.forward(d)
+                continue
+            count += 1
+            r, w, _ = oracle.forward(d)
+            assert oracle.brute(d, (n - 1) ** 2) == (r, w)
+            if n == 2:
+                assert r == 1
+        if n == 2:
+            assert count == 12
+
+
+def test_all_binary_automata_n4_bound():
+    """All 4^8 binary automata on 4 states: forward BFS and brute force
+    agree, and the largest reset threshold is 9 = (n-1)^2 (the Cerny bound
+    holds for 4 states, reached by C_4)."""
+    best = 0
+    for flat in itertools.product(range(4), repeat=8):
+        d = np.array(flat, dtype=np.int32).reshape(2, 4)
+        if not oracle.is_synchronizing(d):
+            continue
+        r, w, _ = oracle.forward(d)
+        if r >= 6:  # brute force where it is cheap to compare the words too
+            assert oracle.brute(d, 9) == (r, w)
+        best = max(best, r)
+    assert best == 9
+
+
+# ---------------------------------------------------------------- invariants
+
+@pytest.mark.parametrize("d", _small_random(25, (8, 36), (2, 3), 37))
+def test_bidirectional_equals_forward(d):
+    r, w, fs = oracle.forward(d)
+    rb, wb, fsb, bsb = oracle.bidir(d)
+    assert (rb, wb) == (r, w)
+    assert fsb == fs[: len(fsb)]
+    assert bsb == oracle.level_sizes(d, 1, len(bsb) - 1)
+    assert len(fsb) - 1 + len(bsb) - 1 == r
+    assert resets(d, wb)
+    n = d.shape[1]
+    assert r <= (n ** 3 - n) // 6  # Frankl-Pin (Section 1.1)
+
+
+@pytest.mark.parametrize("seed", range(10))
+def test_sink_automata_bound(seed):
+    n = 6 + seed
+    d = gen.random_automaton(n, 2, 500 + seed, sink=True)
+    r, w, _ = oracle.forward(d)
+    assert r <= n * (n - 1) // 2  # Section 3.1.1: sink automata
+    assert resets(d, w)
+    s = np.arange(n)
+    for a in w:
+        s = d[a][s]
+    assert set(s.tolist()) == {0}  # a reset word of a sink automaton ends in the sink
+
+
+def test_one_state():
+    d = np.zeros((2, 1), dtype=np.int32)
+    assert oracle.forward(d) == (0, [], [1])
+    assert oracle.bidir(d)[:2] == (0, [])
+    assert oracle.brute(d, 4) == (0, [])
+
+
+def test_rejects_bad_input():
+    with pytest.raises(oracle.OracleError):
+        oracle.forward(np.array([[0, 5]], dtype=np.int32))
+    assert not oracle.is_synchronizing(np.array([[1, 0], [0, 1]], dtype=np.int32))
