@@ -1,0 +1,359 @@
+"""Benchmark: exact-r instances/s of the batched GPU search on one GB300.
+
+Workload (default): a batch of 4096 random binary automata, n uniform in
+[64, 192], delta iid uniform (seeds 0..4095, SplitMix64 recipe of gen.py),
+bitsets of three 64-bit words.  One step solves the whole batch: r and the
+least shortest reset word of every instance.
+
+  value         instances/s of sw_batch_device, automata already in HBM,
+                CUDA events on the search stream; L2 flushed between steps.
+  e2e           the same through sw_batch with host buffers (automata copied
+                in and results copied out inside the timed region).
+  roofline      the meet kernel (the dominant kernel), integer-ALU bound:
+                2W 32-bit LOP3 per (X, Y) pair tested.
+  one_at_a_time sw_reset_threshold in a loop over a sample, and the batched
+                call on the same sample.
+  cpu_baseline  the CPU oracle (bidirectional) on a bounded sample, all cores.
+
+--impl reference times the CPU oracle instead (the reference arm).
+"""
+
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_2207_05495_gb300 import gen  # noqa: E402
+
+PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
+# 32-bit integer logic (LOP3) results per clock per SM on sm_103 (64: 16
+# lanes in each of the 4 SM sub-partitions); see the ALU roofline notes.
+INT32_LANES_PER_SM = 64
+SM_MAX_MHZ_FALLBACK = 2070.0
+N_SMS_NOMINAL = 152
+
+
+def workload(name: str, rank: int = 0):
+    if name == "c3":
+        count = 4096
+        seeds = range(rank * count, (rank + 1) * count)
+        return [gen.random_automaton_ranged(64, 192, 2, s) for s in seeds], {
+            "workload": "batch of 4096 random binary automata, n~U[64,192], k=2, seeds 0..4095, 3x64-bit bitsets",
+            "instances": count, "n_range": [64, 192], "k": 2}
+    if name == "c1":
+        return [gen.random_automaton(40, 2, 0)], {"workload": "single random binary automaton n=40 k=2 seed 0",
+                                                  "instances": 1}
+    if name == "cerny":
+        return [gen.cerny(n) for n in range(16, 29)], {"workload": "Cerny automata n=16..28", "instances": 13}
+    raise SystemExit(f"unknown workload {name}")
+
+
+class Clocks:
+    """nvidia-smi sampling during the timed region."""
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except OSError:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def flush_l2(buf):
+    buf.add_(1)  # touches 256 MiB, larger than the 129 MB L2
+
+
+def cpu_sample(ds, budget_s: float, cores: int):
+    """The oracle (bidirectional BFS) over the first instances of the
+    workload, all cores, until the time budget is spent; instances still
+    running at the hard cap are abandoned and not counted."""
+    import multiprocessing as mp
+    ctx = mp.get_context("spawn")
+    t0 = time.perf_counter()
+    done = 0
+    with ctx.Pool(cores, initializer=_oracle_init) as pool:
+        pending = []
+        nxt = 0
+        while True:
+            while nxt < len(ds) and len(pending) < 2 * cores and time.perf_counter() - t0 < budget_s:
+                pending.append(pool.apply_async(_oracle_one, (ds[nxt],)))
+                nxt += 1
+            still = []
+            for p in pending:
+                if p.ready():
+                    p.get()
+                    done += 1
+                else:
+                    still.append(p)
+            pending = still
+            el = time.perf_counter() - t0
+            if (el >= budget_s and not pending) or el >= 3 * budget_s or (nxt == len(ds) and not pending):
+                break
+            time.sleep(0.01)
+        elapsed = time.perf_counter() - t0
+        pool.terminate()
+    return done, elapsed
+
+
+def _oracle_init():
+    sys.path.insert(0, ROOT)
+
+
+def _oracle_one(d):
+    import oracle
+    return oracle.bidir(d)[0]
+
+
+def run_reference(args, ds, cfg, rank, world):
+    if rank != 0:
+        return
+    cores = os.cpu_count() or 1
+    import oracle
+    oracle.build()
+    for _ in range(args.warmup):
+        cpu_sample(ds, 2.0, cores)
+    tot_done, tot_t = 0, 0.0
+    for _ in range(args.steps):
+        d, t = cpu_sample(ds, args.cpu_budget, cores)
+        tot_done += d
+        tot_t += t
+    v = tot_done / tot_t if tot_t else 0.0
+    sample = f"first instances of the workload in seed order, {args.cpu_budget:.0f} s per step, {cores} processes"
+    line = {"impl": "reference", "metric": "exact-r instances/sec", "value": v, "unit": "instances/s",
+            "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot_t / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
+            "config": cfg,
+            "cpu_baseline": {"value": v, "unit": "instances/s", "cores": cores, "kind": "oracle", "sample": sample},
+            "e2e": {"value": v, "unit": "instances/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="c3", choices=["c3", "c1", "cerny"])
+    ap.add_argument("--ws-gb", type=float, default=96.0)
+    ap.add_argument("--cpu-budget", type=float, default=20.0)
+    ap.add_argument("--one-sample", type=int, default=256)
+    ap.add_argument("--no-cpu", action="store_true")
+    args = ap.parse_args()
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    ds, cfg = workload(args.workload, rank)
+    cfg = dict(cfg)
+    cfg["l2"] = "flushed between steps (256 MiB write)"
+    cfg["parallelism"] = f"replicas x{world} (independent instances per GPU)"
+
+    if args.impl == "reference":
+        run_reference(args, ds, cfg, rank, world)
+        return
+
+    # CPU baseline first: its process pool is spawned before any CUDA work
+    cpu = None
+    if rank == 0 and not args.no_cpu:
+        cores = os.cpu_count() or 1
+        import oracle
+        oracle.build()
+        done, el = cpu_sample(ds, args.cpu_budget, cores)
+        cpu = {"value": done / el if el else 0.0, "unit": "instances/s", "cores": cores, "kind": "oracle",
+               "sample": f"first {done} instances of the workload in seed order (bidirectional oracle, "
+                         f"{cores} processes, {el:.1f} s)"}
+
+    import torch
+    import torch.distributed as dist
+    from paper_2207_05495_gb300 import build, sw
+    build.build()
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+
+    count = len(ds)
+    ns = np.array([d.shape[1] for d in ds], np.int32)
+    ks = np.array([d.shape[0] for d in ds], np.int32)
+    W = int(max((int(n) + 63) // 64 for n in ns))
+    flat = np.concatenate([d.ravel() for d in ds]).astype(np.int32)
+    offs = np.concatenate([[0], np.cumsum([d.size for d in ds])[:-1]]).astype(np.int64)
+    word_cap = 1024
+    word_off = np.arange(count + 1, dtype=np.int64) * word_cap
+    stream = torch.cuda.Stream()
+    ws = sw.workspace(int(args.ws_gb * (1 << 30)))
+    d_delta = torch.from_numpy(flat).cuda()
+    d_r = torch.zeros(count, dtype=torch.int32, device="cuda")
+    d_words = torch.zeros(int(word_off[-1]), dtype=torch.uint8, device="cuda")
+    l2 = torch.zeros(64 << 20, dtype=torch.int32, device="cuda")
+    torch.cuda.synchronize()
+
+    def step():
+        rc = sw.sw_batch_device(ns, ks, d_delta, offs, stream=stream, ws=ws, d_r=d_r, d_words=d_words,
+                                word_off=word_off)
+        if rc != 0:
+            raise RuntimeError(f"sw_batch_device failed: {rc}")
+
+    for _ in range(args.warmup):
+        step()
+    sw.sw_set_timing(True)
+    times, stats = [], []
+    with Clocks(local) as clk:
+        for _ in range(args.steps):
+            flush_l2(l2)
+            torch.cuda.synchronize()
+            barrier()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            step()
+            e1.record(stream)
+            torch.cuda.synchronize()
+            barrier()
+            times.append(e0.elapsed_time(e1))
+            stats.append(sw.sw_last_stats())
+    sw.sw_set_timing(False)
+    ms = float(np.mean(times))
+    if world > 1:
+        t = torch.tensor([ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    value = count * world / (ms * 1e-3)
+
+    # results of the last timed step, checked: every word resets Q
+    r = d_r.cpu().numpy()
+    words = d_words.cpu().numpy()
+    for i in range(count):
+        st = np.arange(ns[i])
+        for a in words[word_off[i]: word_off[i] + r[i]]:
+            st = ds[i][a][st]
+        assert r[i] >= 0 and len(np.unique(st)) == 1, f"instance {i}: word does not reset"
+
+    # end to end: host automata in, host results out, through sw_batch
+    hs = [sw.load(d) for d in ds]
+    e2e_t = []
+    for it in range(args.warmup + args.steps):
+        torch.cuda.synchronize()
+        barrier()
+        t0 = time.perf_counter()
+        rh, wh = sw.sw_batch(hs, stream=stream, ws=ws, word_cap=word_cap)
+        torch.cuda.synchronize()
+        barrier()
+        if it >= args.warmup:
+            e2e_t.append(time.perf_counter() - t0)
+    assert (rh == r).all()
+    e2e_s = float(np.mean(e2e_t))
+    h2d = int(sum(d.size for d in ds) * 2)  # uint16 transition tables
+    d2h = int(4 * count + int(r.sum()))
+
+    # one at a time vs batched, on the same sample
+    m = min(args.one_sample, count)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for i in range(m):
+        sw.sw_reset_threshold(hs[i], stream=stream, ws=ws, word_cap=word_cap)
+    torch.cuda.synchronize()
+    one_s = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    sw.sw_batch(hs[:m], stream=stream, ws=ws, word_cap=word_cap)
+    torch.cuda.synchronize()
+    batch_m_s = time.perf_counter() - t0
+
+    # roofline of the meet kernel
+    st = stats[-1]
+    meet_ms = sum(s["meet_ms"] for s in stats) / len(stats)
+    pairs = sum(s["pairs"] for s in stats) / len(stats)
+    launches = sum(s["meet_launches"] for s in stats) / len(stats)
+    ops = pairs * 2 * W
+    achieved = ops / (meet_ms * 1e-3) / 1e12 if meet_ms > 0 else 0.0
+    props = torch.cuda.get_device_properties(local)
+    clocks = clk.summary()
+    peak = INT32_LANES_PER_SM * props.multi_processor_count * SM_MAX_MHZ_FALLBACK * 1e6 / 1e12
+    line = {
+        "metric": "exact-r instances/sec", "value": value, "unit": "instances/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic", "config": cfg,
+        "e2e": {"value": count * world / e2e_s, "unit": "instances/s", "h2d_bytes_per_step": h2d,
+                "d2h_bytes_per_step": d2h},
+        "roofline": {"bound": "alu", "kernel": "k_meet", "achieved": achieved, "peak": peak, "unit": "Tops/s",
+                     "frac": achieved / peak if peak else None, "traffic": None,
+                     "ops_per_pair": 2 * W, "pairs_per_step": pairs, "launches_per_step": launches,
+                     "avg_launch_ms": meet_ms / max(launches, 1),
+                     "peak_basis": f"{INT32_LANES_PER_SM} int32 lanes/SM x {props.multi_processor_count} SMs x "
+                                   f"{SM_MAX_MHZ_FALLBACK:.0f} MHz"},
+        "subset_checks_per_sec": pairs / (ms * 1e-3),
+        "kernel_ms_per_step": {"meet": meet_ms, "expand": sum(s["expand_ms"] for s in stats) / len(stats),
+                               "compact": sum(s["compact_ms"] for s in stats) / len(stats)},
+        "iterations_per_step": st["iterations"],
+        "one_at_a_time": {"value": m / one_s, "unit": "instances/s", "sample": f"first {m} instances",
+                          "batched_same_sample": m / batch_m_s},
+        "clocks": clocks,
+        "gpu_launches": int(st.get("launches", 0)),
+        "cpu_baseline": cpu,
+    }
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

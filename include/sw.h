@@ -1,0 +1,198 @@
+/*
+ * sw.h - exact reset threshold and least shortest reset word of a
+ * deterministic finite complete automaton, on one GB300 GPU (sm_103a).
+ *
+ * The method is the bidirectional breadth-first search of Szykula and Zyzik,
+ * "An Improved Algorithm for Finding the Shortest Synchronizing Words"
+ * (arXiv 2207.05495), Section 2.1 and Alg. 1: a forward search from Q over
+ * images delta(S, a), an inverse search from the singletons over preimages
+ * delta^{-1}(S, a), every level deduplicated against all sets seen before in
+ * its direction, and after every step the meet condition "some forward set
+ * X lies inside some backward set Y" (Section 2), which proves a reset word
+ * of length (forward depth) + (backward depth).
+ *
+ * Conventions shared by every entry point:
+ *  - An automaton has n states (1 <= n <= SW_MAX_STATES) and k letters
+ *    (1 <= k <= SW_MAX_LETTERS).  Its transition table `delta` is int32
+ *    [k][n], letter-major: delta[a*n + q] = delta(q, a) (Section 1).
+ *  - r is the reset threshold, the length of the shortest reset words
+ *    (Section 1).  The word returned is the lexicographically least reset
+ *    word of length r, letters as indices 0..k-1 (the paper does not fix a
+ *    tie-break; this is the library's reading).  n = 1 gives r = 0.
+ *  - Level i of a direction is the list of distinct sets first reached at
+ *    depth i: forward, images delta(Q, w) with |w| = i; backward, nonempty
+ *    preimages delta^{-1}({q}, w).  Empty preimages are dropped.
+ *  - `stream` is a cudaStream_t (for example torch.cuda.current_stream()
+ *    .cuda_stream); NULL is the legacy default stream.  Every call is
+ *    synchronous: it returns after its work on `stream` has finished.
+ *  - `workspace` is caller-owned device memory of `ws_bytes` bytes (for
+ *    example a torch uint8 tensor); the library keeps no pointer to it after
+ *    the call returns and never frees it.  Its base must be 256-byte
+ *    aligned.  Everything the search stores (levels, parent links, the
+ *    deduplication hash table, candidates) lives in it; when it is too small
+ *    the call fails with SW_ENOMEM and the caller may retry with more.
+ *  - Return value: SW_OK (0) or one of the SW_E* codes below; the same code
+ *    is kept as the calling thread's sw_last_error().
+ *  - Handles are host objects.  One handle must not be used by two calls at
+ *    the same time; different handles may.
+ */
+#ifndef SW_H
+#define SW_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define SW_MAX_STATES 576
+#define SW_MAX_LETTERS 255
+
+enum sw_status {
+    SW_OK = 0,
+    SW_EINVAL = 1,      /* an argument is out of range or a pointer is NULL */
+    SW_ENOTSYNC = 2,    /* the automaton is not synchronizing */
+    SW_ENOMEM = 3,      /* the workspace (or a table in it) is too small */
+    SW_ETIMEOUT = 4,    /* a bounded device-side wait gave up */
+    SW_EWORDCAP = 5,    /* r exceeds the word capacity; r is still written */
+    SW_ECUDA = 6,       /* a CUDA runtime call failed */
+    SW_EBUSY = 7,       /* server: no room for the request right now */
+    SW_EAGAIN = 8,      /* server: no finished request to report */
+    SW_EINTERNAL = 9    /* a self-check of a result failed */
+};
+
+typedef struct sw_automaton *sw_handle;
+
+/*
+ * Validates and copies an automaton (Section 1) into a new host-side
+ * handle.  delta: host int32 [k][n], read during the call only.  Checks
+ * 1 <= n <= SW_MAX_STATES, 1 <= k <= SW_MAX_LETTERS, every entry in [0, n),
+ * and that the automaton is synchronizing by the pair test of Section 2
+ * (every two states can be mapped to one state, O(k n^2) on the host).
+ * Returns NULL on failure (sw_last_error(): SW_EINVAL or SW_ENOTSYNC).
+ * Release with sw_free.
+ */
+sw_handle sw_load_automaton(int32_t n, int32_t k, const int32_t *delta);
+
+/* Releases a handle (NULL is ignored). */
+void sw_free(sw_handle h);
+
+/* The status of the calling thread's last failing call (SW_OK if none). */
+int32_t sw_last_error(void);
+
+/* A static description of a status code. */
+const char *sw_error_string(int32_t code);
+
+/*
+ * Smallest workspace in bytes with which a search of `count` automata of
+ * at most n_max states and k_max letters can start (it may still need more
+ * as its levels grow).
+ */
+size_t sw_workspace_min_bytes(int32_t n_max, int32_t k_max, int32_t count);
+
+/*
+ * Reset threshold and least shortest reset word of one automaton by the
+ * bidirectional search of Alg. 1 (Section 2.1) restricted to deletion of
+ * duplicates and an equality history, with the meet test after every step
+ * (Section 2).  r: host int32, written on SW_OK and on SW_EWORDCAP.
+ * word: host uint8 [word_cap] or NULL; on SW_OK holds the r letters.
+ * Errors: SW_EINVAL, SW_ENOMEM (workspace too small; retry with more),
+ * SW_EWORDCAP (r > word_cap), SW_ECUDA, SW_EINTERNAL (the word failed its
+ * on-device check |delta(Q, word)| = 1).
+ */
+int32_t sw_reset_threshold(sw_handle h, void *stream, void *workspace, size_t ws_bytes,
+                           int32_t *r, uint8_t *word, int32_t word_cap);
+
+/*
+ * Per-level sizes of the last search that included `h` (single or batched):
+ * fwd[i] = size of forward level i for i < *nf, bwd[j] = size of backward
+ * level j for j < *nb.  The search computes forward levels 0..i and
+ * backward levels 0..j with i + j = r; which split it takes depends on the
+ * direction rule, but every computed level's size is a property of the
+ * automaton alone.  At most fwd_cap / bwd_cap entries are written; *nf and
+ * *nb are the full counts.  Host pointers.  SW_EINVAL if h has not been
+ * searched.
+ */
+int32_t sw_level_sizes(sw_handle h, int64_t *fwd, int32_t fwd_cap, int32_t *nf, int64_t *bwd,
+                       int32_t bwd_cap, int32_t *nb);
+
+/*
+ * Batched search of `count` automata (Section 2.1, as sw_reset_threshold):
+ * all instances advance together, one level per iteration, so that each
+ * kernel launch serves every unfinished instance.  hs: host array of
+ * handles.  r_out: host int32 [count]; r_out[i] = r of hs[i], or -1 if that
+ * instance failed.  words: host uint8 [words_cap] or NULL; instance i's word
+ * is written at words + word_off[i] and may use word_off[i+1] - word_off[i]
+ * bytes (word_off: host int64 [count + 1], nondecreasing, word_off[count] <=
+ * words_cap).  Returns SW_OK when every instance succeeded, else the first
+ * failing instance's code (the others' results are still written).  When
+ * the workspace cannot hold all instances at once, they are run in waves.
+ */
+int32_t sw_batch(const sw_handle *hs, int32_t count, void *stream, void *workspace,
+                 size_t ws_bytes, int32_t *r_out, uint8_t *words, const int64_t *word_off,
+                 int64_t words_cap);
+
+/*
+ * As sw_batch, with the automata and the results in device memory: d_delta
+ * is device int32, instance i's table [k[i]][n[i]] starting at element
+ * delta_off[i]; n, k, delta_off: host arrays [count].  d_r: device int32
+ * [count]; d_words: device uint8 [words_cap] laid out by word_off (host
+ * int64 [count + 1]) as in sw_batch.  The automata are not checked for
+ * synchronizability up front; a non-synchronizing one ends with r = -1 and
+ * SW_ENOTSYNC when one of its searches runs out of new sets.
+ */
+int32_t sw_batch_device(int32_t count, const int32_t *n, const int32_t *k,
+                        const int32_t *d_delta, const int64_t *delta_off, void *stream,
+                        void *workspace, size_t ws_bytes, int32_t *d_r, uint8_t *d_words,
+                        const int64_t *word_off, int64_t words_cap);
+
+/*
+ * Counters of the calling thread's last search (sw_reset_threshold,
+ * sw_batch or sw_batch_device), for throughput and roofline reporting.
+ * Any pointer may be NULL.
+ *   pairs:        (X, Y) pairs tested by the meet kernel (Section 2 meet
+ *                 condition), excluding tiles skipped after a meet.
+ *   candidates:   sets produced by the image/preimage kernel.
+ *   iterations:   search iterations (each advances every unfinished
+ *                 instance by one level).
+ *   meet_ms, expand_ms, compact_ms: summed device time of those kernels,
+ *                 from CUDA events on the search's stream (only when timing
+ *                 was enabled by sw_set_timing(1)).
+ *   meet_launches: launches of the meet kernel.
+ *   launches:     launches of all of the library's kernels.
+ */
+int32_t sw_last_stats(int64_t *pairs, int64_t *candidates, int32_t *iterations,
+                      double *meet_ms, double *expand_ms, double *compact_ms,
+                      int32_t *meet_launches, int64_t *launches);
+
+/* Enables (1) or disables (0) per-kernel CUDA-event timing for later
+ * searches on the calling thread. */
+void sw_set_timing(int32_t on);
+
+/*
+ * Tunable parameters (all have defaults; values out of range are clamped).
+ *   meet_rows_per_thread: forward sets each meet thread keeps in registers
+ *                         (1, 2, 4 or 8; 0 = pick by word count).
+ *   meet_b_tile:          backward sets per shared-memory tile (even).
+ *   dir_theta:            a forward step is taken when its predicted cost is
+ *                         at most dir_theta times the backward step's.
+ *   set_cost:             cost of producing one set, in pair tests (the
+ *                         paper's SetCost, Section 2.1.2).
+ * Applies to later searches on the calling thread.
+ */
+typedef struct sw_options {
+    int32_t meet_rows_per_thread;
+    int32_t meet_b_tile;
+    double dir_theta;
+    double set_cost;
+} sw_options;
+
+void sw_get_options(sw_options *opt);
+void sw_set_options(const sw_options *opt);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SW_H */

@@ -1,0 +1,627 @@
+// Device kernels of the bidirectional subset search (Section 2.1, Alg. 1).
+//
+// A subset of Q is stored as W 64-bit words (state q at bit q%64 of word
+// q/64; bits >= n are zero).  All levels of all instances and both
+// directions live in one arena of sets; each stored set has a parent link
+// ((parent arena index) << 8 | letter) and an owner tag (instance << 1 |
+// direction).  One open-addressing hash table over the arena holds, per
+// (instance, direction), every set seen so far: it removes duplicates
+// within a level and sets of earlier levels (the equality history).
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace sw {
+
+constexpr uint64_t kEmpty = ~0ull;
+constexpr uint64_t kCand = 1ull << 62;  // slot value kCand + c: candidate c (this expansion)
+constexpr int kScanBlock = 1024;        // candidates per block in flag/compact
+constexpr int kScanThreads = 256;
+constexpr int kMaxProbe = 1 << 14;
+
+enum : uint32_t { kStatusTableFull = 1u, kStatusWordFail = 2u, kStatusVerifyFail = 4u };
+
+struct ExpandJob {
+    int64_t cand_off;    // first candidate id
+    int64_t parent_off;  // arena index of the parent level's first set
+    int64_t parent_cnt;
+    int64_t delta_off;   // instance's uint16 [k][n] table in delta16
+    int32_t owner;       // instance << 1 | direction (0 forward, 1 backward)
+    int32_t n, k, pad;
+};
+
+struct MeetJob {
+    int64_t f_off, f_cnt, b_off, b_cnt;
+    int64_t tile_off;    // first tile id of this job
+    int64_t ntb;         // tiles along B
+    int64_t slot;        // index into best[]
+};
+
+struct RootJob {
+    int64_t arena_off;   // F_0 = {Q} here, then the n singletons
+    int32_t inst, n;
+};
+
+struct WordJob {
+    int64_t f_arena;     // arena index of the meeting forward set X
+    int64_t blev;        // first (offset, count) pair of B_0..B_{j-1} in blevels
+    int64_t word_off;    // output position in the word buffer
+    int64_t delta_off;
+    int32_t i, j, n, k;
+    int32_t slot;        // index into word_status[]
+    int32_t pad;
+};
+
+// ------------------------------------------------------------ small helpers
+
+__device__ __forceinline__ uint64_t fmix64(uint64_t x) {
+    // MurmurHash3 finalizer (Appleby), a published 64-bit mixer
+    x ^= x >> 33;
+    x *= 0xff51afd7ed558ccdull;
+    x ^= x >> 33;
+    x *= 0xc4ceb9fe1a85ec53ull;
+    x ^= x >> 33;
+    return x;
+}
+
+template <int W>
+__device__ __forceinline__ uint64_t hash_set(uint32_t owner, const uint64_t (&s)[W]) {
+    uint64_t h = fmix64(0x9E3779B97F4A7C15ull * (owner + 1u));
+#pragma unroll
+    for (int w = 0; w < W; ++w) h = fmix64(h ^ (s[w] + 0x632BE59BD9B4E019ull * (w + 1)));
+    return h;
+}
+
+__device__ __forceinline__ uint64_t ld_relaxed(const uint64_t *p) {
+    uint64_t v;
+    asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+    return v;
+}
+
+__device__ __forceinline__ uint32_t ld_relaxed32(const uint32_t *p) {
+    uint32_t v;
+    asm volatile("ld.relaxed.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+template <int W>
+__device__ __forceinline__ void load_set(const uint64_t *__restrict__ p, uint64_t (&s)[W]) {
+#pragma unroll
+    for (int w = 0; w < W; ++w) s[w] = p[w];
+}
+
+// bit t of a set held in registers (t < 64 W), without dynamic indexing
+template <int W>
+__device__ __forceinline__ uint32_t get_bit(const uint64_t (&s)[W], uint32_t t) {
+    uint64_t word = s[0];
+#pragma unroll
+    for (int w = 1; w < W; ++w) word = ((t >> 6) == (uint32_t)w) ? s[w] : word;
+    return (uint32_t)(word >> (t & 63)) & 1u;
+}
+
+// Image delta(S, a) (Section 2): scatter every set bit of S through delta.
+template <int W>
+__device__ __forceinline__ void image(const uint64_t (&S)[W], const uint16_t *__restrict__ da,
+                                      uint64_t (&T)[W]) {
+#pragma unroll
+    for (int w = 0; w < W; ++w) T[w] = 0;
+#pragma unroll
+    for (int w = 0; w < W; ++w) {
+        uint64_t s = S[w];
+        while (s) {
+            int b = __ffsll((long long)s) - 1;
+            s &= s - 1;
+            uint32_t t = __ldg(da + w * 64 + b);
+            uint64_t bit = 1ull << (t & 63);
+            uint32_t tw = t >> 6;
+#pragma unroll
+            for (int v = 0; v < W; ++v) T[v] |= (tw == (uint32_t)v) ? bit : 0ull;
+        }
+    }
+}
+
+// Preimage delta^{-1}(S, a) (Section 2): state p is in it iff S holds delta(p, a).
+template <int W>
+__device__ __forceinline__ void preimage(const uint64_t (&S)[W], const uint16_t *__restrict__ da,
+                                         int n, uint64_t (&T)[W]) {
+#pragma unroll
+    for (int w = 0; w < W; ++w) {
+        uint64_t acc = 0;
+        int base = w * 64;
+        int lim = n - base < 64 ? n - base : 64;
+        for (int b = 0; b < lim; ++b) acc |= (uint64_t)get_bit<W>(S, __ldg(da + base + b)) << b;
+        T[w] = acc;
+    }
+}
+
+template <int W>
+__device__ __forceinline__ bool set_equal(const uint64_t (&a)[W], const uint64_t *__restrict__ p) {
+    bool eq = true;
+#pragma unroll
+    for (int w = 0; w < W; ++w) eq &= (a[w] == p[w]);
+    return eq;
+}
+
+template <int W>
+__device__ __forceinline__ bool set_equal_cg(const uint64_t (&a)[W], const uint64_t *p) {
+    bool eq = true;
+#pragma unroll
+    for (int w = 0; w < W; ++w) eq &= (a[w] == __ldcg(p + w));
+    return eq;
+}
+
+__device__ __forceinline__ int find_job_expand(const ExpandJob *__restrict__ jobs, int njobs, int64_t c) {
+    int lo = 0, hi = njobs - 1;
+    while (lo < hi) {
+        int mid = (lo + hi + 1) >> 1;
+        if (jobs[mid].cand_off <= c) lo = mid; else hi = mid - 1;
+    }
+    return lo;
+}
+
+// ------------------------------------------------------------ roots
+
+// F_0 = {Q} and B_0 = the n singletons of each new instance (Alg. 1,
+// initialisation), stored and entered into the table.  One thread per set.
+template <int W>
+__global__ void k_roots(const RootJob *__restrict__ jobs, int njobs, uint64_t *__restrict__ sets,
+                        uint64_t *__restrict__ link, uint32_t *__restrict__ owner,
+                        uint64_t *__restrict__ table, uint64_t cap_table, uint32_t *status) {
+    const RootJob J = jobs[blockIdx.y];
+    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t <= J.n; t += gridDim.x * blockDim.x) {
+        uint64_t s[W];
+        uint32_t own;
+        if (t == 0) {  // Q: the first n bits
+#pragma unroll
+            for (int w = 0; w < W; ++w) {
+                int lo = w * 64;
+                s[w] = (J.n >= lo + 64) ? ~0ull : (J.n > lo ? ((1ull << (J.n - lo)) - 1) : 0ull);
+            }
+            own = (uint32_t)J.inst << 1;
+        } else {
+            int q = t - 1;
+#pragma unroll
+            for (int w = 0; w < W; ++w) s[w] = ((q >> 6) == w) ? (1ull << (q & 63)) : 0ull;
+            own = ((uint32_t)J.inst << 1) | 1u;
+        }
+        int64_t g = J.arena_off + t;
+#pragma unroll
+        for (int w = 0; w < W; ++w) sets[g * W + w] = s[w];
+        link[g] = ~0ull;
+        owner[g] = own;
+        uint64_t pos = __umul64hi(hash_set<W>(own, s), cap_table);
+        int probe = 0;
+        for (; probe < kMaxProbe; ++probe) {
+            unsigned long long old = atomicCAS((unsigned long long *)(table + pos), kEmpty, (unsigned long long)g);
+            if (old == kEmpty) break;
+            pos = (pos + 1 == cap_table) ? 0 : pos + 1;
+        }
+        if (probe == kMaxProbe) atomicOr(status, kStatusTableFull);
+    }
+}
+
+// ------------------------------------------------------------ expand + insert
+
+// CalculateImages / CalculatePreimages (Alg. 1) fused with duplicate
+// removal and the equality history: candidate c = p*k + a of a job is the
+// image (forward) or preimage (backward) of parent p under letter a.  It is
+// written to cand_sets and entered into the table; among equal sets of one
+// (instance, direction) the smallest candidate id keeps the slot
+// (atomicMin), and a set already stored (an earlier level) is dropped.
+// cand_slot[c] = its slot, or -1 when dropped (duplicate of history, empty
+// preimage, or table overflow, which also raises kStatusTableFull).
+template <int W>
+__global__ void __launch_bounds__(256) k_expand(
+    const ExpandJob *__restrict__ jobs, int njobs, int64_t ncand, const uint16_t *__restrict__ delta16,
+    const uint64_t *__restrict__ sets, const uint32_t *__restrict__ owner, uint64_t *table,
+    uint64_t cap_table, uint64_t *cand_sets, uint32_t *cand_owner, int64_t *__restrict__ cand_slot,
+    uint32_t *status) {
+    for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < ncand;
+         c += (int64_t)gridDim.x * blockDim.x) {
+        const ExpandJob &J = jobs[find_job_expand(jobs, njobs, c)];
+        int64_t local = c - J.cand_off;
+        int64_t p = local / J.k;
+        int a = (int)(local - p * J.k);
+        uint64_t S[W], T[W];
+        load_set<W>(sets + (J.parent_off + p) * W, S);
+        const uint16_t *da = delta16 + J.delta_off + (int64_t)a * J.n;
+        const uint32_t own = (uint32_t)J.owner;
+        if ((own & 1u) == 0) image<W>(S, da, T);
+        else preimage<W>(S, da, J.n, T);
+        bool empty = true;
+#pragma unroll
+        for (int w = 0; w < W; ++w) empty &= (T[w] == 0);
+        if (empty) {  // only preimages can be empty; they contain no nonempty set
+            cand_slot[c] = -1;
+            continue;
+        }
+#pragma unroll
+        for (int w = 0; w < W; ++w) cand_sets[c * W + w] = T[w];
+        cand_owner[c] = own;
+        __threadfence();  // publish the set before its id can be seen in the table
+        const uint64_t me = kCand + (uint64_t)c;
+        uint64_t pos = __umul64hi(hash_set<W>(own, T), cap_table);
+        int64_t result = -1;
+        int probe = 0;
+        for (; probe < kMaxProbe; ++probe) {
+            uint64_t *slot = table + pos;
+            uint64_t v = ld_relaxed(slot);
+            if (v == kEmpty) {
+                unsigned long long old = atomicCAS((unsigned long long *)slot, kEmpty, (unsigned long long)me);
+                if (old == kEmpty) { result = (int64_t)pos; break; }
+                v = old;
+            }
+            __threadfence();  // order the reads of v's set after observing v
+            if (v < kCand) {  // a stored set (earlier level or earlier kernel)
+                if (owner[v] == own && set_equal<W>(T, sets + v * W)) break;  // seen before: drop
+            } else {
+                uint64_t c2 = v - kCand;
+                if (ld_relaxed32(cand_owner + c2) == own && set_equal_cg<W>(T, cand_sets + c2 * W)) {
+                    atomicMin((unsigned long long *)slot, (unsigned long long)me);
+                    result = (int64_t)pos;
+                    break;
+                }
+            }
+            pos = (pos + 1 == cap_table) ? 0 : pos + 1;
+        }
+        if (probe == kMaxProbe) atomicOr(status, kStatusTableFull);
+        cand_slot[c] = result;
+    }
+}
+
+// ------------------------------------------------------------ flag / scan / compact
+
+// A candidate survives when it still owns its slot (it is the first of its
+// set in this level and the set was not seen before).  flag[c] = 1 then;
+// block_cnt[b] = survivors of block b.
+__global__ void __launch_bounds__(kScanThreads) k_flag_count(int64_t ncand, const int64_t *__restrict__ cand_slot,
+                                                             const uint64_t *__restrict__ table,
+                                                             uint8_t *__restrict__ flag, uint32_t *__restrict__ block_cnt) {
+    constexpr int IPT = kScanBlock / kScanThreads;
+    int64_t base = (int64_t)blockIdx.x * kScanBlock + threadIdx.x * IPT;
+    uint32_t cnt = 0;
+#pragma unroll
+    for (int i = 0; i < IPT; ++i) {
+        int64_t c = base + i;
+        uint8_t f = 0;
+        if (c < ncand) {
+            int64_t s = cand_slot[c];
+            f = (s >= 0 && table[s] == kCand + (uint64_t)c) ? 1 : 0;
+            flag[c] = f;
+        }
+        cnt += f;
+    }
+    __shared__ uint32_t red[kScanThreads / 32];
+    for (int o = 16; o; o >>= 1) cnt += __shfl_xor_sync(0xffffffffu, cnt, o);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = cnt;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        uint32_t t = 0;
+        for (int i = 0; i < kScanThreads / 32; ++i) t += red[i];
+        block_cnt[blockIdx.x] = t;
+    }
+}
+
+// Exclusive scan of the per-block counts in one CTA of 1024 threads;
+// block_off[nblocks] = total.
+__global__ void __launch_bounds__(1024) k_scan_blocks(int64_t nblocks, const uint32_t *__restrict__ block_cnt,
+                                                      uint64_t *__restrict__ block_off) {
+    __shared__ uint64_t warp_sum[32];
+    __shared__ uint64_t carry;
+    if (threadIdx.x == 0) carry = 0;
+    __syncthreads();
+    for (int64_t base = 0; base < nblocks; base += 1024) {
+        int64_t i = base + threadIdx.x;
+        uint64_t v = (i < nblocks) ? block_cnt[i] : 0;
+        uint64_t x = v;  // inclusive warp scan
+        for (int o = 1; o < 32; o <<= 1) {
+            uint64_t y = __shfl_up_sync(0xffffffffu, x, o);
+            if ((threadIdx.x & 31) >= o) x += y;
+        }
+        if ((threadIdx.x & 31) == 31) warp_sum[threadIdx.x >> 5] = x;
+        __syncthreads();
+        if (threadIdx.x < 32) {
+            uint64_t s = warp_sum[threadIdx.x];
+            for (int o = 1; o < 32; o <<= 1) {
+                uint64_t y = __shfl_up_sync(0xffffffffu, s, o);
+                if (threadIdx.x >= o) s += y;
+            }
+            warp_sum[threadIdx.x] = s;  // inclusive over warps
+        }
+        __syncthreads();
+        uint64_t before = carry + (threadIdx.x >= 32 ? warp_sum[(threadIdx.x >> 5) - 1] : 0) + x - v;
+        if (i < nblocks) block_off[i] = before;
+        __syncthreads();
+        if (threadIdx.x == 1023) carry = before + v;
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) block_off[nblocks] = carry;
+}
+
+// Survivors, in candidate order (= the canonical (parent, letter) order),
+// are appended to the arena at arena_top + their rank; their parent link and
+// owner are stored and their table slot is switched from the candidate id to
+// the arena index.  job_rank[J] = rank of job J's first candidate.
+template <int W>
+__global__ void __launch_bounds__(kScanThreads) k_compact(
+    const ExpandJob *__restrict__ jobs, int njobs, int64_t ncand, const uint8_t *__restrict__ flag,
+    const uint64_t *__restrict__ block_off, const uint64_t *__restrict__ cand_sets,
+    const uint32_t *__restrict__ cand_owner, const int64_t *__restrict__ cand_slot, uint64_t *__restrict__ table,
+    int64_t arena_top, uint64_t *__restrict__ sets, uint64_t *__restrict__ link, uint32_t *__restrict__ owner,
+    uint64_t *__restrict__ job_rank) {
+    constexpr int IPT = kScanBlock / kScanThreads;
+    int64_t base = (int64_t)blockIdx.x * kScanBlock + threadIdx.x * IPT;
+    uint8_t f[IPT];
+    uint32_t cnt = 0;
+#pragma unroll
+    for (int i = 0; i < IPT; ++i) {
+        f[i] = (base + i < ncand) ? flag[base + i] : 0;
+        cnt += f[i];
+    }
+    // exclusive block scan of cnt
+    uint32_t x = cnt;
+    for (int o = 1; o < 32; o <<= 1) {
+        uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+        if ((threadIdx.x & 31) >= o) x += y;
+    }
+    __shared__ uint32_t ws[kScanThreads / 32];
+    if ((threadIdx.x & 31) == 31) ws[threadIdx.x >> 5] = x;
+    __syncthreads();
+    uint32_t wbefore = 0;
+    for (int i = 0; i < (int)(threadIdx.x >> 5); ++i) wbefore += ws[i];
+    uint64_t rank = block_off[blockIdx.x] + wbefore + x - cnt;
+#pragma unroll
+    for (int i = 0; i < IPT; ++i) {
+        int64_t c = base + i;
+        if (c >= ncand) break;
+        int ji = find_job_expand(jobs, njobs, c);
+        const ExpandJob &J = jobs[ji];
+        if (c == J.cand_off) job_rank[ji] = rank;
+        if (f[i]) {
+            int64_t g = arena_top + (int64_t)rank;
+            int64_t local = c - J.cand_off;
+            int64_t p = local / J.k;
+            int64_t a = local - p * J.k;
+#pragma unroll
+            for (int w = 0; w < W; ++w) sets[g * W + w] = cand_sets[c * W + w];
+            link[g] = ((uint64_t)(J.parent_off + p) << 8) | (uint64_t)a;
+            owner[g] = cand_owner[c];
+            table[cand_slot[c]] = (uint64_t)g;
+            ++rank;
+        }
+    }
+}
+
+// ------------------------------------------------------------ meet check
+
+// Meet condition (Section 2): is some forward set X = F[f] inside some
+// backward set Y = B[b], i.e. X & ~Y == 0 on every word?  Per job the
+// smallest such f is wanted (it gives the least reset word); best[slot]
+// = min over found pairs of (f << 32 | b).
+//
+// The F x B pair space of every job is cut into tiles of TF = NT*R forward
+// rows by tb backward rows, numbered F-major so that low f come first.
+// Each thread keeps R forward sets in registers as 32-bit halves; the
+// backward tile sits in shared memory word-major (word w of set i at
+// sB[w*tb + i]) so that one 16-byte broadcast load gives word w of two
+// backward sets.  A pair costs 2W three-input LOP3 steps
+// acc |= f & ~y and one compare, accumulated into a per-row hit flag; the
+// rare hit is located by a second pass.  A tile whose first row is beyond
+// the best f already found is skipped.
+template <int W, int R, int NT>
+__global__ void __launch_bounds__(NT) k_meet(const MeetJob *__restrict__ jobs, int njobs, int64_t ntiles,
+                                             int tb, const uint64_t *__restrict__ sets,
+                                             unsigned long long *best, unsigned long long *pairs_done) {
+    extern __shared__ __align__(16) uint64_t sB[];  // [W][tb]
+    __shared__ int64_t s_job;
+    __shared__ int s_skip;
+    constexpr int TF = NT * R;
+    unsigned long long my_pairs = 0;
+    for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+        if (threadIdx.x == 0) {
+            int lo = 0, hi = njobs - 1;
+            while (lo < hi) {
+                int mid = (lo + hi + 1) >> 1;
+                if (jobs[mid].tile_off <= tile) lo = mid; else hi = mid - 1;
+            }
+            s_job = lo;
+            const MeetJob &J = jobs[lo];
+            int64_t local = tile - J.tile_off;
+            int64_t tf = local / J.ntb;
+            unsigned long long cur = *(volatile unsigned long long *)(best + J.slot);
+            s_skip = ((int64_t)(cur >> 32) < tf * TF) ? 1 : 0;
+        }
+        __syncthreads();
+        if (s_skip) { __syncthreads(); continue; }
+        const MeetJob &J = jobs[s_job];
+        int64_t local = tile - J.tile_off;
+        int64_t tf = local / J.ntb;
+        int64_t tbi = local - tf * J.ntb;
+        int64_t f0 = tf * TF;
+        int64_t b0 = tbi * tb;
+        int nb = (int)min((int64_t)tb, J.b_cnt - b0);
+        // backward tile -> shared memory, word-major; rows nb..(even) are empty sets
+        const uint64_t *gB = sets + (J.b_off + b0) * W;
+        int nbe = (nb + 1) & ~1;
+        for (int e = threadIdx.x; e < nbe * W; e += NT) {
+            int i = e / W, w = e - i * W;
+            sB[w * tb + i] = (i < nb) ? gB[e] : 0ull;
+        }
+        // forward rows -> registers
+        uint32_t f[R][2 * W];
+        bool valid[R];
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+            int64_t row = f0 + r * NT + threadIdx.x;
+            valid[r] = row < J.f_cnt;
+            const uint64_t *p = sets + (J.f_off + (valid[r] ? row : 0)) * W;
+#pragma unroll
+            for (int w = 0; w < W; ++w) {
+                uint64_t v = p[w];
+                f[r][2 * w] = (uint32_t)v;
+                f[r][2 * w + 1] = (uint32_t)(v >> 32);
+            }
+        }
+        __syncthreads();
+        bool hit[R];
+#pragma unroll
+        for (int r = 0; r < R; ++r) hit[r] = false;
+        for (int i = 0; i < nbe; i += 2) {
+            uint32_t y0[2 * W], y1[2 * W];
+#pragma unroll
+            for (int w = 0; w < W; ++w) {
+                uint4 v = *reinterpret_cast<const uint4 *>(sB + w * tb + i);
+                y0[2 * w] = v.x; y0[2 * w + 1] = v.y;
+                y1[2 * w] = v.z; y1[2 * w + 1] = v.w;
+            }
+#pragma unroll
+            for (int r = 0; r < R; ++r) {
+                uint32_t a0 = f[r][0] & ~y0[0];
+                uint32_t a1 = f[r][0] & ~y1[0];
+#pragma unroll
+                for (int h = 1; h < 2 * W; ++h) {
+                    a0 |= f[r][h] & ~y0[h];
+                    a1 |= f[r][h] & ~y1[h];
+                }
+                hit[r] |= (a0 == 0) | (a1 == 0);
+            }
+        }
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+            if (hit[r] && valid[r]) {  // rare: find the first b of this row
+                for (int i = 0; i < nb; ++i) {
+                    uint32_t acc = 0;
+#pragma unroll
+                    for (int w = 0; w < W; ++w) {
+                        uint64_t y = sB[w * tb + i];
+                        acc |= (f[r][2 * w] & ~(uint32_t)y) | (f[r][2 * w + 1] & ~(uint32_t)(y >> 32));
+                    }
+                    if (acc == 0) {
+                        unsigned long long key = ((unsigned long long)(f0 + r * NT + threadIdx.x) << 32) |
+                                                 (unsigned long long)(b0 + i);
+                        atomicMin(best + J.slot, key);
+                        break;
+                    }
+                }
+            }
+        }
+        if (threadIdx.x == 0) {
+            int64_t rows = min((int64_t)TF, J.f_cnt - f0);
+            my_pairs += (unsigned long long)rows * (unsigned long long)nb;
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0 && my_pairs) atomicAdd(pairs_done, my_pairs);
+}
+
+// ------------------------------------------------------------ word recovery
+
+// One CTA per met instance.  The prefix x is the forward parent chain of the
+// meeting set X (the predecessor pointers of Section 2).  The suffix y is
+// the least word of length j mapping X to one state: letter by letter, the
+// smallest a such that delta(S, a) lies inside some set of B_m, m = the
+// letters still to come (a set inside a depth-m backward set is exactly a
+// set that m more letters can map to one state, and by minimality of r that
+// backward set was first reached at depth m).  Finally |delta(Q, xy)| = 1 is
+// checked.  word_status[slot]: 0 ok, else kStatusWordFail/kStatusVerifyFail.
+template <int W, int NT>
+__global__ void __launch_bounds__(NT) k_words(const WordJob *__restrict__ jobs,
+                                              const int64_t *__restrict__ blevels,
+                                              const uint16_t *__restrict__ delta16,
+                                              const uint64_t *__restrict__ sets,
+                                              const uint64_t *__restrict__ link, uint8_t *__restrict__ words,
+                                              uint32_t *__restrict__ word_status) {
+    const WordJob J = jobs[blockIdx.x];
+    uint8_t *out = words + J.word_off;
+    __shared__ int s_choice;
+    __shared__ uint32_t s_fail;
+    if (threadIdx.x == 0) {
+        s_fail = 0;
+        uint64_t g = (uint64_t)J.f_arena;
+        for (int d = J.i - 1; d >= 0; --d) {
+            uint64_t l = link[g];
+            out[d] = (uint8_t)(l & 0xFF);
+            g = l >> 8;
+        }
+    }
+    uint64_t S[W];
+    load_set<W>(sets + J.f_arena * W, S);
+    __syncthreads();
+    for (int t = 0; t < J.j; ++t) {
+        int m = J.j - 1 - t;
+        int64_t off = blevels[2 * (J.blev + m)], cnt = blevels[2 * (J.blev + m) + 1];
+        if (threadIdx.x == 0) s_choice = -1;
+        __syncthreads();
+        for (int a = 0; a < J.k; ++a) {
+            uint64_t T[W];
+            image<W>(S, delta16 + J.delta_off + (int64_t)a * J.n, T);
+            int found = 0;
+            for (int64_t b = threadIdx.x; b < cnt; b += NT) {
+                const uint64_t *y = sets + (off + b) * W;
+                uint64_t acc = 0;
+#pragma unroll
+                for (int w = 0; w < W; ++w) acc |= T[w] & ~y[w];
+                if (acc == 0) { found = 1; break; }
+            }
+            if (__syncthreads_or(found)) {
+                if (threadIdx.x == 0) s_choice = a;
+                __syncthreads();
+                break;
+            }
+        }
+        int a = s_choice;
+        if (a < 0) {
+            if (threadIdx.x == 0) s_fail = kStatusWordFail;
+            break;
+        }
+        uint64_t T[W];
+        image<W>(S, delta16 + J.delta_off + (int64_t)a * J.n, T);
+#pragma unroll
+        for (int w = 0; w < W; ++w) S[w] = T[w];
+        if (threadIdx.x == 0) out[J.i + t] = (uint8_t)a;
+        __syncthreads();
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        uint32_t st = s_fail;
+        if (!st) {  // verify: delta(Q, word) is a singleton
+            uint64_t Q[W], T[W];
+#pragma unroll
+            for (int w = 0; w < W; ++w) {
+                int lo = w * 64;
+                Q[w] = (J.n >= lo + 64) ? ~0ull : (J.n > lo ? ((1ull << (J.n - lo)) - 1) : 0ull);
+            }
+            for (int t = 0; t < J.i + J.j; ++t) {
+                image<W>(Q, delta16 + J.delta_off + (int64_t)out[t] * J.n, T);
+#pragma unroll
+                for (int w = 0; w < W; ++w) Q[w] = T[w];
+            }
+            int pc = 0;
+#pragma unroll
+            for (int w = 0; w < W; ++w) pc += __popcll(Q[w]);
+            if (pc != 1) st = kStatusVerifyFail;
+        }
+        word_status[J.slot] = st;
+    }
+}
+
+// int32 [k][n] tables -> uint16 (device-resident input path); one CTA row
+// (blockIdx.y) per instance.
+struct ConvJob {
+    int64_t src_off, dst_off, count;
+    int32_t n, pad;
+};
+
+__global__ void k_delta_to_u16(const ConvJob *__restrict__ jobs, const int32_t *__restrict__ src,
+                               uint16_t *__restrict__ dst, uint32_t *bad) {
+    const ConvJob J = jobs[blockIdx.y];
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < J.count;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        int32_t v = src[J.src_off + i];
+        if (v < 0 || v >= J.n) atomicOr(bad, 1u);
+        dst[J.dst_off + i] = (uint16_t)(v < 0 || v >= J.n ? 0 : v);
+    }
+}
+
+}  // namespace sw

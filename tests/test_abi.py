@@ -1,0 +1,84 @@
+"""The C-ABI library builds, loads and exports every declared entry point;
+its host-side validation works without a GPU."""
+
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+from paper_2207_05495_gb300 import build, gen, sw
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_functions():
+    text = open(os.path.join(ROOT, "include", "sw.h")).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(sw_[a-z_]+)\s*\(", text)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    build.build()
+    return sw.lib()
+
+
+def test_exports_every_declared_symbol(lib):
+    names = declared_functions()
+    assert "sw_reset_threshold" in names and "sw_batch" in names
+    raw = ctypes.CDLL(build.LIB)
+    for name in names:
+        assert hasattr(raw, name), name
+
+
+def test_error_strings(lib):
+    assert lib.sw_error_string(0) == b"ok"
+    assert b"not synchronizing" in lib.sw_error_string(2)
+
+
+def test_load_validates_without_gpu(lib):
+    d = gen.random_automaton(20, 2, 1)
+    h = sw.load(d)
+    assert h.n == 20 and h.k == 2
+    with pytest.raises(sw.SwError) as e:
+        sw.load(np.array([[1, 0], [0, 1]], dtype=np.int32))  # two permutations
+    assert e.value.code == sw.SW_ENOTSYNC
+    with pytest.raises(sw.SwError) as e:
+        sw.load(np.array([[0, 2]], dtype=np.int32))
+    assert e.value.code == sw.SW_EINVAL
+    with pytest.raises(sw.SwError) as e:
+        sw.sw_load_automaton(sw.SW_MAX_STATES + 1, 1, np.zeros((1, sw.SW_MAX_STATES + 1), np.int32))
+    assert e.value.code == sw.SW_EINVAL
+    with pytest.raises(sw.SwError) as e:
+        sw.sw_level_sizes(h)  # never searched
+    assert e.value.code == sw.SW_EINVAL
+
+
+def test_load_agrees_with_generator_filter(lib):
+    rng = np.random.default_rng(5)
+    for _ in range(300):
+        n = int(rng.integers(2, 9))
+        d = rng.integers(0, n, size=(2, n)).astype(np.int32)
+        ok = gen.is_synchronizing(d)
+        if ok:
+            sw.load(d)
+        else:
+            with pytest.raises(sw.SwError):
+                sw.load(d)
+
+
+def test_workspace_min_bytes(lib):
+    a = sw.sw_workspace_min_bytes(40, 2, 1)
+    b = sw.sw_workspace_min_bytes(192, 2, 4096)
+    assert 0 < a < b
+    assert sw.sw_workspace_min_bytes(0, 2, 1) == 0
+
+
+def test_options_roundtrip(lib):
+    o = sw.sw_get_options()
+    assert o.dir_theta == 1.0 and o.set_cost == 512.0
+    o.dir_theta = -3.0  # invalid: reset to the default
+    sw.sw_set_options(o)
+    assert sw.sw_get_options().dir_theta == 1.0

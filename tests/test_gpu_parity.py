@@ -1,0 +1,178 @@
+"""GPU results against the CPU oracle, element by element: r, the least
+reset word and every computed level size must be identical (all integer).
+Calls go through the C-ABI (Python binding of include/sw.h)."""
+
+import json
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2207_05495_gb300 import gen
+
+pytestmark = pytest.mark.gpu
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+@pytest.fixture(scope="module")
+def sw():
+    import torch
+    assert torch.cuda.is_available()
+    from paper_2207_05495_gb300 import build, sw as swmod
+    build.build()
+    return swmod
+
+
+@pytest.fixture(scope="module")
+def ws(sw):
+    return sw.workspace(512 << 20)
+
+
+def resets(delta, word):
+    states = np.arange(delta.shape[1])
+    for a in word:
+        states = delta[a][states]
+    return len(np.unique(states)) == 1
+
+
+def check_sizes(delta, fs, bs):
+    assert fs == oracle.level_sizes(delta, 0, len(fs) - 1)
+    assert bs == oracle.level_sizes(delta, 1, len(bs) - 1)
+    assert len(fs) - 1 + len(bs) - 1 >= 0
+
+
+def test_hand_examples(sw, ws):
+    for ex in json.load(open(os.path.join(GOLDEN, "hand_examples.json")))["examples"]:
+        d = np.array(ex["delta"], dtype=np.int32)
+        h = sw.load(d)
+        r, w = sw.sw_reset_threshold(h, ws=ws)
+        assert (r, w) == (ex["r"], ex["word"]), ex["name"]
+        fs, bs = sw.sw_level_sizes(h)
+        assert fs == ex["fwd_sizes"][: len(fs)] and bs == ex["bwd_sizes"][: len(bs)], ex["name"]
+        assert len(fs) + len(bs) - 2 == r
+
+
+def test_single_random_n40_seed0(sw, ws):
+    d = gen.random_automaton(40, 2, 0)
+    h = sw.load(d)
+    r, w = sw.sw_reset_threshold(h, ws=ws)
+    ro, wo, fo = oracle.forward(d)
+    assert (r, w) == (ro, wo)
+    fs, bs = sw.sw_level_sizes(h)
+    assert fs == fo[: len(fs)]
+    check_sizes(d, fs, bs)
+
+
+@pytest.mark.parametrize("n", list(range(1, 29)))
+def test_cerny(sw, ws, n):
+    d = gen.cerny(n)
+    h = sw.load(d)
+    r, w = sw.sw_reset_threshold(h, ws=ws)
+    assert r == (n - 1) ** 2
+    assert w == ([] if n == 1 else [1] + ([0] * (n - 1) + [1]) * (n - 2))
+    fs, bs = sw.sw_level_sizes(h)
+    if n <= 20:
+        check_sizes(d, fs, bs)
+
+
+def _random_cases():
+    cases = []
+    rng = np.random.default_rng(2024)
+    for i in range(60):
+        n = int(rng.integers(2, 70))
+        k = int(rng.choice([1, 2, 2, 3, 4]))
+        cases.append((n, k, 7000 + i))
+    return cases
+
+
+@pytest.mark.parametrize("n,k,seed", _random_cases())
+def test_random_vs_oracle(sw, ws, n, k, seed):
+    d = gen.random_automaton(n, k, seed)
+    h = sw.load(d)
+    r, w = sw.sw_reset_threshold(h, ws=ws)
+    ro, wo, fo, bo = oracle.bidir(d)
+    assert (r, w) == (ro, wo)
+    assert resets(d, w)
+    fs, bs = sw.sw_level_sizes(h)
+    check_sizes(d, fs, bs)
+
+
+def test_batch_equals_single(sw, ws):
+    ds = [gen.random_automaton(int(n), 2, 300 + i) for i, n in enumerate([5, 17, 33, 64, 65, 40, 2, 1, 90, 128])]
+    hs = [sw.load(d) for d in ds]
+    rb, wb = sw.sw_batch(hs, ws=ws)
+    sizes_b = [sw.sw_level_sizes(h) for h in hs]
+    for i, d in enumerate(ds):
+        r, w = sw.sw_reset_threshold(hs[i], ws=ws)
+        assert (rb[i], wb[i]) == (r, w)
+        ro, wo, _, _ = oracle.bidir(d)
+        assert (r, w) == (ro, wo)
+        fs, bs = sizes_b[i]
+        check_sizes(d, fs, bs)
+
+
+def test_w_boundaries_and_max_states(sw, ws):
+    # n = 64 (Q fills a word), 65 (one bit in a second word), 576 (nine words)
+    for n in (63, 64, 65, 128, 129):
+        d = gen.random_automaton(n, 2, 11 + n)
+        r, w = sw.sw_reset_threshold(sw.load(d), ws=ws)
+        assert (r, w) == oracle.bidir(d)[:2]
+    n = 576
+    halve = np.arange(n) // 2
+    perm = np.random.default_rng(1).permutation(n)
+    d = np.stack([perm, halve]).astype(np.int32)
+    h = sw.load(d)
+    r, w = sw.sw_reset_threshold(h, ws=ws)
+    ro, wo, fo = oracle.forward(d)
+    assert (r, w) == (ro, wo) and r == 10
+    fs, bs = sw.sw_level_sizes(h)
+    check_sizes(d, fs, bs)
+
+
+def test_word_cap_and_small_workspace(sw, ws):
+    d = gen.cerny(6)
+    h = sw.load(d)
+    with pytest.raises(sw.SwError) as e:
+        sw.sw_reset_threshold(h, ws=ws, word_cap=10)
+    assert e.value.code == sw.SW_EWORDCAP
+    tiny = sw.workspace(300 << 10)
+    d = gen.random_automaton(150, 2, 3)
+    with pytest.raises(sw.SwError) as e:
+        sw.sw_reset_threshold(sw.load(d), ws=tiny)
+    assert e.value.code == sw.SW_ENOMEM
+
+
+def test_batch_device_matches_host_batch(sw, ws):
+    import torch
+    ds = [gen.random_automaton_ranged(20, 80, 2, s) for s in range(40)]
+    ns = [d.shape[1] for d in ds]
+    ks = [d.shape[0] for d in ds]
+    flat = np.concatenate([d.ravel() for d in ds]).astype(np.int32)
+    offs = np.cumsum([0] + [d.size for d in ds[:-1]]).astype(np.int64)
+    d_delta = torch.from_numpy(flat).cuda()
+    d_r = torch.zeros(len(ds), dtype=torch.int32, device="cuda")
+    cap = 256
+    word_off = np.arange(len(ds) + 1, dtype=np.int64) * cap
+    d_words = torch.zeros(int(word_off[-1]), dtype=torch.uint8, device="cuda")
+    rc = sw.sw_batch_device(ns, ks, d_delta, offs, ws=ws, d_r=d_r, d_words=d_words, word_off=word_off)
+    assert rc == 0
+    rb, wb = sw.sw_batch([sw.load(d) for d in ds], ws=ws)
+    r_dev = d_r.cpu().numpy()
+    words_dev = d_words.cpu().numpy()
+    assert (r_dev == rb).all()
+    for i in range(len(ds)):
+        assert words_dev[word_off[i]: word_off[i] + r_dev[i]].tolist() == wb[i]
+
+
+def test_batch_device_not_synchronizing(sw, ws):
+    import torch
+    good = gen.random_automaton(12, 2, 1)
+    bad = np.array([[1, 2, 0], [0, 1, 2]], dtype=np.int32)  # two permutations
+    flat = np.concatenate([good.ravel(), bad.ravel()]).astype(np.int32)
+    d_delta = torch.from_numpy(flat).cuda()
+    d_r = torch.zeros(2, dtype=torch.int32, device="cuda")
+    rc = sw.sw_batch_device([12, 3], [2, 2], d_delta, [0, good.size], ws=ws, d_r=d_r)
+    assert rc == sw.SW_ENOTSYNC
+    r = d_r.cpu().tolist()
+    assert r[1] == -1 and r[0] == oracle.forward(good)[0]
