@@ -189,10 +189,11 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="c3", choices=["c3", "c1", "cerny"])
-    ap.add_argument("--ws-gb", type=float, default=96.0)
+    ap.add_argument("--ws-gb", type=float, default=160.0)
     ap.add_argument("--cpu-budget", type=float, default=20.0)
     ap.add_argument("--one-sample", type=int, default=256)
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--count", type=int, default=0, help="use only the first COUNT instances (small cases)")
     args = ap.parse_args()
 
     rank = int(os.environ.get("RANK", "0"))
@@ -200,6 +201,10 @@ def main():
     local = int(os.environ.get("LOCAL_RANK", "0"))
     ds, cfg = workload(args.workload, rank)
     cfg = dict(cfg)
+    if args.count and args.count < len(ds):
+        ds = ds[: args.count]
+        cfg["workload"] += f" (first {args.count} only)"
+        cfg["instances"] = args.count
     cfg["l2"] = "flushed between steps (256 MiB write)"
     cfg["parallelism"] = f"replicas x{world} (independent instances per GPU)"
 
@@ -250,7 +255,9 @@ def main():
         rc = sw.sw_batch_device(ns, ks, d_delta, offs, stream=stream, ws=ws, d_r=d_r, d_words=d_words,
                                 word_off=word_off)
         if rc != 0:
-            raise RuntimeError(f"sw_batch_device failed: {rc}")
+            bad = (d_r.cpu().numpy() < 0).nonzero()[0]
+            raise RuntimeError(f"sw_batch_device failed: {rc}; failed instances {bad[:20].tolist()} "
+                               f"n={ns[bad[:20]].tolist()} stats={sw.sw_last_stats()}")
 
     for _ in range(args.warmup):
         step()
@@ -342,7 +349,8 @@ def main():
         "subset_checks_per_sec": pairs / (ms * 1e-3),
         "kernel_ms_per_step": {"meet": meet_ms, "expand": sum(s["expand_ms"] for s in stats) / len(stats),
                                "compact": sum(s["compact_ms"] for s in stats) / len(stats)},
-        "iterations_per_step": st["iterations"],
+        "iterations_per_step": st["iterations"], "waves": st["waves"], "evictions": st["evictions"],
+        "arena_peak_sets": st["arena_peak"],
         "one_at_a_time": {"value": m / one_s, "unit": "instances/s", "sample": f"first {m} instances",
                           "batched_same_sample": m / batch_m_s},
         "clocks": clocks,

@@ -161,10 +161,16 @@ int32_t sw_batch_device(int32_t count, const int32_t *n, const int32_t *k,
  *                 was enabled by sw_set_timing(1)).
  *   meet_launches: launches of the meet kernel.
  *   launches:     launches of all of the library's kernels.
+ *   waves:        waves the instances were run in (1 when all fitted).
+ *   evictions:    instances set back to a later wave for lack of room.
+ *   arena_peak:   most sets stored at once (all instances of a wave).
+ *   and_iters:    warp-wide AND steps of the bitmap meet kernel (each ANDs
+ *                 one 2048-bit state bitmap into the running intersection).
  */
 int32_t sw_last_stats(int64_t *pairs, int64_t *candidates, int32_t *iterations,
                       double *meet_ms, double *expand_ms, double *compact_ms,
-                      int32_t *meet_launches, int64_t *launches);
+                      int32_t *meet_launches, int64_t *launches, int32_t *waves,
+                      int32_t *evictions, int64_t *arena_peak, int64_t *and_iters);
 
 /* Enables (1) or disables (0) per-kernel CUDA-event timing for later
  * searches on the calling thread. */
@@ -172,9 +178,16 @@ void sw_set_timing(int32_t on);
 
 /*
  * Tunable parameters (all have defaults; values out of range are clamped).
- *   meet_rows_per_thread: forward sets each meet thread keeps in registers
- *                         (1, 2, 4 or 8; 0 = pick by word count).
- *   meet_b_tile:          backward sets per shared-memory tile (even).
+ *   meet_algo:            0 = vertical bitmaps (default): the backward
+ *                         chunk is transposed to one bitmap per state and a
+ *                         forward set X meets set b iff bit b survives the AND
+ *                         of the bitmaps of X's states; 1 = direct test
+ *                         X & ~Y == 0 on every pair (LOP3).
+ *   meet_rows_per_thread: direct test: forward sets each thread keeps in
+ *                         registers (1, 2, 4 or 8; 0 = pick by word count).
+ *   meet_b_tile:          direct test: backward sets per shared-memory tile
+ *                         (even).
+ *   meet_f_rows:          bitmap test: forward sets per tile (0 = 2048).
  *   dir_theta:            a forward step is taken when its predicted cost is
  *                         at most dir_theta times the backward step's.
  *   set_cost:             cost of producing one set, in pair tests (the
@@ -182,8 +195,10 @@ void sw_set_timing(int32_t on);
  * Applies to later searches on the calling thread.
  */
 typedef struct sw_options {
+    int32_t meet_algo;
     int32_t meet_rows_per_thread;
     int32_t meet_b_tile;
+    int32_t meet_f_rows;
     double dir_theta;
     double set_cost;
 } sw_options;

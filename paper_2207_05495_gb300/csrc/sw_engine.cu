@@ -36,11 +36,14 @@ struct Stats {
     int32_t iterations = 0;
     double meet_ms = 0, expand_ms = 0, compact_ms = 0;
     int32_t meet_launches = 0;
+    int64_t and_iters = 0;  // bitmap meet: warp-wide AND steps
     int64_t launches = 0;  // every kernel launch of the search
+    int32_t waves = 0, evictions = 0;
+    int64_t arena_peak = 0;  // most sets stored at once
 };
 
 thread_local int32_t g_last_error = SW_OK;
-thread_local sw_options g_opt = {0, 0, 1.0, 512.0};
+thread_local sw_options g_opt = {0, 0, 0, 0, 1.0, 16384.0};
 thread_local bool g_timing = false;
 thread_local Stats g_stats;
 
@@ -143,7 +146,7 @@ struct Layout {
     unsigned long long *best;
     uint32_t *word_status;
     uint32_t *status;
-    unsigned long long *pairs;
+    unsigned long long *pairs;  // [0] pairs tested, [1] bitmap AND steps
     uint8_t *word_area;
     int64_t word_area_cap;
     uint16_t *delta16;
@@ -193,7 +196,7 @@ size_t small_area_bytes(int32_t count, int64_t delta_elems) {
     add(c * sizeof(unsigned long long));
     add(c * sizeof(uint32_t));
     add(sizeof(uint32_t));
-    add(sizeof(unsigned long long));
+    add(2 * sizeof(unsigned long long));
     add(std::max<size_t>(c * 512, 1 << 20));  // word area
     add((size_t)delta_elems * sizeof(uint16_t));
     return b;
@@ -212,7 +215,7 @@ bool carve(void *ws, size_t bytes, int W, int32_t count, int64_t delta_elems, in
     L.best = cv.take<unsigned long long>(c);
     L.word_status = cv.take<uint32_t>(c);
     L.status = cv.take<uint32_t>(1);
-    L.pairs = cv.take<unsigned long long>(1);
+    L.pairs = cv.take<unsigned long long>(2);
     L.word_area_cap = (int64_t)std::max<size_t>(c * 512, 1 << 20);
     L.word_area = cv.take<uint8_t>((size_t)L.word_area_cap);
     L.delta16 = cv.take<uint16_t>((size_t)std::max<int64_t>(delta_elems, 1));
@@ -269,7 +272,9 @@ int default_rows(int W) { return W == 1 ? 8 : (W <= 3 ? 4 : 2); }
 int default_btile(int W) { return std::max(64, (4096 / W) & ~1); }
 
 struct MeetCfg {
+    int algo;  // 0 vertical bitmaps, 1 direct LOP3 test
     int R, tb, nt;
+    int tf_rows;  // forward rows per tile (bitmap kernel)
 };
 
 MeetCfg meet_cfg(int W) {
@@ -284,6 +289,10 @@ MeetCfg meet_cfg(int W) {
     int max_tb = (96 * 1024 / (8 * W)) & ~1;
     c.tb = std::min(tb, max_tb);
     c.nt = 256;
+    c.algo = g_opt.meet_algo == 1 ? 1 : 0;
+    if (c.algo == 0) c.tb = kBmRows;
+    c.tf_rows = g_opt.meet_f_rows > 0 ? g_opt.meet_f_rows : 2048;
+    c.tf_rows = std::max(8, std::min(c.tf_rows, 1 << 20));
     return c;
 }
 
@@ -304,6 +313,26 @@ cudaError_t launch_meet_r(const MeetJob *jobs, int njobs, int64_t ntiles, int tb
     int64_t grid = (int64_t)sm_count() * std::max(per_sm, 1);
     grid = std::min<int64_t>(grid, ntiles);
     kern<<<(unsigned)grid, NT, smem, st>>>(jobs, njobs, ntiles, tb, sets, best, pairs);
+    return cudaGetLastError();
+}
+
+template <int W>
+cudaError_t launch_meet_bm(const MeetJob *jobs, int njobs, int64_t ntiles, int tf_rows, const uint64_t *sets,
+                           unsigned long long *best, unsigned long long *pairs, unsigned long long *iters,
+                           cudaStream_t st) {
+    constexpr int NT = 256;
+    auto kern = k_meet_bm<W, NT>;
+    size_t smem = (size_t)64 * W * kBmStride * sizeof(uint32_t);
+    static thread_local bool configured = false;
+    if (!configured) {
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        configured = true;
+    }
+    int per_sm = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, NT, smem);
+    int64_t grid = std::min<int64_t>((int64_t)sm_count() * std::max(per_sm, 1), ntiles);
+    kern<<<(unsigned)grid, NT, smem, st>>>(jobs, njobs, ntiles, tf_rows, sets, best, pairs, iters);
     return cudaGetLastError();
 }
 
@@ -335,6 +364,8 @@ struct Ops {
     }
     static cudaError_t meet(int nj, int64_t ntiles, const MeetCfg &c, const Layout &L, cudaStream_t st) {
         g_stats.launches++;
+        if (c.algo == 0)
+            return launch_meet_bm<W>(L.mjobs, nj, ntiles, c.tf_rows, L.sets, L.best, L.pairs, L.pairs + 1, st);
         switch (c.R) {
             case 1:
                 if constexpr (W >= 3) return launch_meet_r<W, 1>(L.mjobs, nj, ntiles, c.tb, L.sets, L.best, L.pairs, st);
@@ -430,6 +461,8 @@ struct Search {
         mc = meet_cfg(W);
     }
 
+    int64_t top_peak() const { return top; }
+
     int choose_dir(const Inst &x) const {
         double F = (double)x.cnt[0].back(), B = (double)x.cnt[1].back(), k = x.k;
         double cF = g_opt.set_cost * k * F + k * (1.0 - x.dupl[0]) * F * B;
@@ -439,6 +472,7 @@ struct Search {
 
     // Starts a wave: clears the table and stores the roots of `wave`.
     int start_wave(const std::vector<int> &wave) {
+        g_stats.waves++;
         top = 0;
         stored_total = 0;
         CK(cudaMemsetAsync(L.table, 0xFF, L.cap_table * sizeof(uint64_t), st));
@@ -506,19 +540,16 @@ struct Search {
         }
         if (who.empty()) {
             // nothing fits: give up the instance holding the most sets; it
-            // is retried in a later wave (alone if need be)
+            // is retried in a later wave (the wave loop fails it only if it
+            // ran alone)
             auto it = std::max_element(active.begin(), active.end(),
                                        [&](int a, int b) { return I[a].stored < I[b].stored; });
             int id = *it;
             active.erase(it);
-            if (active.empty() && I[id].evictions > 0) {
-                I[id].state = kFailed;
-                I[id].code = SW_ENOMEM;
-            } else {
-                I[id].state = kWaiting;
-                I[id].evictions++;
-                evicted.push_back(id);
-            }
+            I[id].state = kWaiting;
+            I[id].evictions++;
+            g_stats.evictions++;
+            evicted.push_back(id);
             return SW_OK;
         }
         int nj = (int)who.size();
@@ -573,7 +604,7 @@ struct Search {
             int nm = (int)advanced.size();
             MeetJob *mj = (MeetJob *)g_up.get(nm * sizeof(MeetJob));
             if (!mj) return SW_ECUDA;
-            const int64_t TF = (int64_t)mc.nt * mc.R;
+            const int64_t TF = mc.algo == 0 ? (int64_t)mc.tf_rows : (int64_t)mc.nt * mc.R;
             int64_t ntiles = 0;
             for (int t = 0; t < nm; ++t) {
                 Inst &x = I[advanced[t]];
@@ -589,18 +620,19 @@ struct Search {
             }
             CK(cudaMemcpyAsync(L.mjobs, mj, nm * sizeof(MeetJob), cudaMemcpyHostToDevice, st));
             CK(cudaMemsetAsync(L.best, 0xFF, nm * sizeof(unsigned long long), st));
-            CK(cudaMemsetAsync(L.pairs, 0, sizeof(unsigned long long), st));
+            CK(cudaMemsetAsync(L.pairs, 0, 2 * sizeof(unsigned long long), st));
             if (g_timing) CK(cudaEventRecord(g_ev.ev[3], st));
             CK(ops.meet(nm, ntiles, mc, L, st));
             if (g_timing) CK(cudaEventRecord(g_ev.ev[4], st));
             g_stats.meet_launches++;
-            unsigned long long *bd = (unsigned long long *)g_down.get((nm + 1) * sizeof(unsigned long long));
+            unsigned long long *bd = (unsigned long long *)g_down.get((nm + 2) * sizeof(unsigned long long));
             if (!bd) return SW_ECUDA;
             CK(cudaMemcpyAsync(bd, L.best, nm * sizeof(unsigned long long), cudaMemcpyDeviceToHost, st));
-            CK(cudaMemcpyAsync(bd + nm, L.pairs, sizeof(unsigned long long), cudaMemcpyDeviceToHost, st));
+            CK(cudaMemcpyAsync(bd + nm, L.pairs, 2 * sizeof(unsigned long long), cudaMemcpyDeviceToHost, st));
             CK(cudaStreamSynchronize(st));
             if (g_timing) g_stats.meet_ms += elapsed(g_ev.ev[3], g_ev.ev[4]);
             g_stats.pairs += (int64_t)bd[nm];
+            g_stats.and_iters += (int64_t)bd[nm + 1];
             for (int t = 0; t < nm; ++t)
                 if (bd[t] != ~0ull) {
                     met.push_back(advanced[t]);
@@ -741,21 +773,23 @@ struct Search {
             std::vector<int> active = wave, evicted;
             while (!active.empty()) {
                 rc = iterate(active, evicted);
-                if (rc == SW_ENOMEM) {  // table overflow: retry the unfinished ones alone later
+                if (rc == SW_ENOMEM) {  // table overflow: retry the unfinished ones later
                     for (int id : active) {
-                        if (I[id].evictions > 0 && active.size() == 1) {
-                            I[id].state = kFailed;
-                            I[id].code = SW_ENOMEM;
-                        } else {
-                            I[id].state = kWaiting;
-                            I[id].evictions++;
-                            evicted.push_back(id);
-                        }
+                        I[id].state = kWaiting;
+                        I[id].evictions++;
+                        g_stats.evictions++;
+                        evicted.push_back(id);
                     }
                     active.clear();
                     break;
                 }
                 if (rc) return rc;
+            }
+            g_stats.arena_peak = std::max(g_stats.arena_peak, top_peak());
+            if (wave.size() == 1 && !evicted.empty()) {  // it had the whole workspace
+                I[evicted[0]].state = kFailed;
+                I[evicted[0]].code = SW_ENOMEM;
+                evicted.clear();
             }
             if (!evicted.empty()) limit = std::max<size_t>(1, std::min(limit, wave.size()) / 2);
             queue = evicted;
@@ -1024,7 +1058,8 @@ int32_t sw_batch_device(int32_t count, const int32_t *n, const int32_t *k, const
 }
 
 int32_t sw_last_stats(int64_t *pairs, int64_t *candidates, int32_t *iterations, double *meet_ms,
-                      double *expand_ms, double *compact_ms, int32_t *meet_launches, int64_t *launches) {
+                      double *expand_ms, double *compact_ms, int32_t *meet_launches, int64_t *launches,
+                      int32_t *waves, int32_t *evictions, int64_t *arena_peak, int64_t *and_iters) {
     if (pairs) *pairs = g_stats.pairs;
     if (candidates) *candidates = g_stats.candidates;
     if (iterations) *iterations = g_stats.iterations;
@@ -1033,6 +1068,10 @@ int32_t sw_last_stats(int64_t *pairs, int64_t *candidates, int32_t *iterations, 
     if (compact_ms) *compact_ms = g_stats.compact_ms;
     if (meet_launches) *meet_launches = g_stats.meet_launches;
     if (launches) *launches = g_stats.launches;
+    if (waves) *waves = g_stats.waves;
+    if (evictions) *evictions = g_stats.evictions;
+    if (arena_peak) *arena_peak = g_stats.arena_peak;
+    if (and_iters) *and_iters = g_stats.and_iters;
     return SW_OK;
 }
 
@@ -1046,8 +1085,10 @@ void sw_set_options(const sw_options *opt) {
     if (!opt) return;
     g_opt = *opt;
     if (!(g_opt.dir_theta > 0) || !std::isfinite(g_opt.dir_theta)) g_opt.dir_theta = 1.0;
-    if (!(g_opt.set_cost >= 0) || !std::isfinite(g_opt.set_cost)) g_opt.set_cost = 512.0;
+    if (!(g_opt.set_cost >= 0) || !std::isfinite(g_opt.set_cost)) g_opt.set_cost = 16384.0;
     if (g_opt.meet_b_tile < 0) g_opt.meet_b_tile = 0;
+    if (g_opt.meet_algo != 1) g_opt.meet_algo = 0;
+    if (g_opt.meet_f_rows < 0) g_opt.meet_f_rows = 0;
 }
 
 }  // extern "C"

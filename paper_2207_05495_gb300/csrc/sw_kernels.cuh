@@ -515,6 +515,131 @@ __global__ void __launch_bounds__(NT) k_meet(const MeetJob *__restrict__ jobs, i
     if (threadIdx.x == 0 && my_pairs) atomicAdd(pairs_done, my_pairs);
 }
 
+// Meet check by vertical bitmaps.  A backward chunk of up to 2048 sets
+// B[b0 .. b0+2047] is transposed into shared memory as one bitmap per state:
+// bit b of M_q is set iff state q lies in B[b0 + b].  Then X is inside
+// B[b0 + b] iff bit b survives the AND of M_q over the states q of X.  A
+// warp takes one forward set X at a time; lane l holds bits 64l..64l+63 of
+// the running AND and the warp stops as soon as every lane is zero (after
+// about five states of X on random instances, against 2W LOP3 per pair for
+// the direct test).  Rows of F are taken in increasing order, so the first
+// survivor of a warp is its least meeting f; a tile whose first row lies
+// beyond the best f found so far is skipped.
+//
+// Shared layout: 32-bit words, M_q's word g (rows 32g..32g+31) at
+// sT[q * kBmStride + g]; the stride 66 keeps the transposing stores at most
+// 2-way bank conflicted and the 64-bit loads of the AND loop aligned.
+constexpr int kBmRows = 2048;   // backward sets per chunk
+constexpr int kBmStride = 66;   // 32-bit words per state row (64 used)
+
+// 32x32 bit transpose across a warp: lane j holds row j on entry (bit i =
+// entry (j, i)); on exit lane i holds column i (bit j = entry (j, i)).
+__device__ __forceinline__ uint32_t warp_transpose32(uint32_t v, int lane) {
+    const uint32_t lo[5] = {0x0000FFFFu, 0x00FF00FFu, 0x0F0F0F0Fu, 0x33333333u, 0x55555555u};
+#pragma unroll
+    for (int st = 0; st < 5; ++st) {
+        const int s = 16 >> st;
+        uint32_t o = __shfl_xor_sync(0xffffffffu, v, s);
+        v = (lane & s) ? ((v & ~lo[st]) | ((o & ~lo[st]) >> s)) : ((v & lo[st]) | ((o & lo[st]) << s));
+    }
+    return v;
+}
+
+template <int W, int NT>
+__global__ void __launch_bounds__(NT) k_meet_bm(const MeetJob *__restrict__ jobs, int njobs, int64_t ntiles,
+                                                int tf_rows, const uint64_t *__restrict__ sets,
+                                                unsigned long long *best, unsigned long long *pairs_done,
+                                                unsigned long long *and_iters) {
+    extern __shared__ __align__(16) uint32_t sT[];  // [64 W][kBmStride]
+    __shared__ int64_t s_job;
+    __shared__ int s_skip;
+    __shared__ unsigned long long s_best;
+    constexpr int NW = NT / 32;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    unsigned long long my_pairs = 0, my_iters = 0;
+    for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+        if (threadIdx.x == 0) {
+            int lo = 0, hi = njobs - 1;
+            while (lo < hi) {
+                int mid = (lo + hi + 1) >> 1;
+                if (jobs[mid].tile_off <= tile) lo = mid; else hi = mid - 1;
+            }
+            s_job = lo;
+            const MeetJob &J = jobs[lo];
+            int64_t tf = (tile - J.tile_off) / J.ntb;
+            unsigned long long cur = *(volatile unsigned long long *)(best + J.slot);
+            s_best = cur;
+            s_skip = ((int64_t)(cur >> 32) < tf * tf_rows) ? 1 : 0;
+        }
+        __syncthreads();
+        if (s_skip) { __syncthreads(); continue; }
+        const MeetJob &J = jobs[s_job];
+        const int64_t local = tile - J.tile_off;
+        const int64_t tf = local / J.ntb;
+        const int64_t b0 = (local - tf * J.ntb) * kBmRows;
+        const int nb = (int)min((int64_t)kBmRows, J.b_cnt - b0);
+        const int64_t f0 = tf * tf_rows;
+        const int64_t f1 = min(f0 + tf_rows, J.f_cnt);
+        // 1. transpose the backward chunk: group g = rows 32g..32g+31
+        for (int g = warp; g < kBmRows / 32; g += NW) {
+            int row = g * 32 + lane;
+            uint64_t y[W];
+            if (row < nb) load_set<W>(sets + (J.b_off + b0 + row) * W, y);
+            else {
+#pragma unroll
+                for (int w = 0; w < W; ++w) y[w] = 0;
+            }
+#pragma unroll
+            for (int h = 0; h < 2 * W; ++h) {
+                uint32_t v = (h & 1) ? (uint32_t)(y[h >> 1] >> 32) : (uint32_t)y[h >> 1];
+                uint32_t c = warp_transpose32(v, lane);  // column lane: state 32h + lane
+                sT[(32 * h + lane) * kBmStride + g] = c;
+            }
+        }
+        __syncthreads();
+        // 2. forward rows, one per warp at a time, in increasing order
+        const int lim = nb - 64 * lane;
+        const uint64_t lane_mask = lim >= 64 ? ~0ull : (lim > 0 ? ((1ull << lim) - 1) : 0ull);
+        for (int64_t f = f0 + warp; f < f1; f += NW) {
+            // lane 0 reads the shared best; the whole warp follows its decision
+            int stop = (int64_t)(*(volatile unsigned long long *)&s_best >> 32) < f;
+            if (__shfl_sync(0xffffffffu, stop, 0)) break;
+            uint64_t x[W];
+            load_set<W>(sets + (J.f_off + f) * W, x);
+            uint64_t acc = lane_mask;
+            bool alive = true;
+#pragma unroll
+            for (int w = 0; w < W; ++w) {
+                uint64_t bits = x[w];
+                while (bits && alive) {
+                    int q = w * 64 + __ffsll((long long)bits) - 1;
+                    bits &= bits - 1;
+                    acc &= *reinterpret_cast<const uint64_t *>(sT + q * kBmStride + 2 * lane);
+                    ++my_iters;
+                    alive = __any_sync(0xffffffffu, acc != 0);
+                }
+            }
+            my_pairs += (unsigned long long)nb;
+            if (alive) {  // every state of X processed: X lies inside the surviving sets
+                unsigned ball = __ballot_sync(0xffffffffu, acc != 0);
+                if (lane == __ffs(ball) - 1) {
+                    unsigned long long key = ((unsigned long long)f << 32) |
+                                             (unsigned long long)(b0 + 64 * lane + __ffsll((long long)acc) - 1);
+                    atomicMin(&s_best, key);
+                    atomicMin(best + J.slot, key);
+                }
+                break;  // later rows of this warp cannot give a smaller f
+            }
+        }
+        __syncthreads();
+    }
+    // per-warp counters: lanes counted the same rows and iterations
+    if (lane == 0) {
+        if (my_pairs) atomicAdd(pairs_done, my_pairs);
+        if (my_iters) atomicAdd(and_iters, my_iters);
+    }
+}
+
 // ------------------------------------------------------------ word recovery
 
 // One CTA per met instance.  The prefix x is the forward parent chain of the

@@ -29,6 +29,17 @@ def ws(sw):
     return sw.workspace(512 << 20)
 
 
+@pytest.fixture(params=[0, 1], ids=["bitmap", "lop3"])
+def meet_algo(sw, request):
+    """Runs a test under both meet kernels (vertical bitmaps, direct LOP3)."""
+    old = sw.sw_get_options()
+    o = sw.sw_get_options()
+    o.meet_algo = request.param
+    sw.sw_set_options(o)
+    yield request.param
+    sw.sw_set_options(old)
+
+
 def resets(delta, word):
     states = np.arange(delta.shape[1])
     for a in word:
@@ -42,7 +53,7 @@ def check_sizes(delta, fs, bs):
     assert len(fs) - 1 + len(bs) - 1 >= 0
 
 
-def test_hand_examples(sw, ws):
+def test_hand_examples(sw, ws, meet_algo):
     for ex in json.load(open(os.path.join(GOLDEN, "hand_examples.json")))["examples"]:
         d = np.array(ex["delta"], dtype=np.int32)
         h = sw.load(d)
@@ -65,7 +76,7 @@ def test_single_random_n40_seed0(sw, ws):
 
 
 @pytest.mark.parametrize("n", list(range(1, 29)))
-def test_cerny(sw, ws, n):
+def test_cerny(sw, ws, meet_algo, n):
     d = gen.cerny(n)
     h = sw.load(d)
     r, w = sw.sw_reset_threshold(h, ws=ws)
@@ -87,7 +98,7 @@ def _random_cases():
 
 
 @pytest.mark.parametrize("n,k,seed", _random_cases())
-def test_random_vs_oracle(sw, ws, n, k, seed):
+def test_random_vs_oracle(sw, ws, meet_algo, n, k, seed):
     d = gen.random_automaton(n, k, seed)
     h = sw.load(d)
     r, w = sw.sw_reset_threshold(h, ws=ws)
@@ -112,7 +123,7 @@ def test_batch_equals_single(sw, ws):
         check_sizes(d, fs, bs)
 
 
-def test_w_boundaries_and_max_states(sw, ws):
+def test_w_boundaries_and_max_states(sw, ws, meet_algo):
     # n = 64 (Q fills a word), 65 (one bit in a second word), 576 (nine words)
     for n in (63, 64, 65, 128, 129):
         d = gen.random_automaton(n, 2, 11 + n)
