@@ -10,7 +10,11 @@ least shortest reset word of every instance.
   e2e           the same through sw_batch with host buffers (automata copied
                 in and results copied out inside the timed region).
   roofline      the meet kernel (the dominant kernel), integer-ALU bound:
-                2W 32-bit LOP3 per (X, Y) pair tested.
+                int32 operations it performs (64 per warp-wide 64-bit AND
+                step, 25 per 32-bit word of each transposed backward row)
+                against 128 int32 lanes/SM x SMs x maximum SM clock.
+  serving       sw_server under Poisson arrivals (n~U[32,128], k in 2..4)
+                at 0.8x the batched capacity: p50/p99 latency, instances/s.
   one_at_a_time sw_reset_threshold in a loop over a sample, and the batched
                 call on the same sample.
   cpu_baseline  the CPU oracle (bidirectional) on a bounded sample, all cores.
@@ -36,9 +40,11 @@ sys.path.insert(0, ROOT)
 from paper_2207_05495_gb300 import gen  # noqa: E402
 
 PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
-# 32-bit integer logic (LOP3) results per clock per SM on sm_103 (64: 16
-# lanes in each of the 4 SM sub-partitions); see the ALU roofline notes.
-INT32_LANES_PER_SM = 64
+# 32-bit integer logic (LOP3) results per clock per SM on sm_103: 4 SM
+# sub-partitions x 32 lanes (a LOP3 issue probe measured 113/clk/SM with its
+# loop overhead included).  Shared memory: 32 banks x 4 B per clock per SM.
+INT32_LANES_PER_SM = 128
+SMEM_BYTES_PER_CLK_SM = 128
 SM_MAX_MHZ_FALLBACK = 2070.0
 N_SMS_NOMINAL = 152
 
@@ -182,6 +188,63 @@ def run_reference(args, ds, cfg, rank, world):
     print(json.dumps(line), flush=True)
 
 
+def serve_bench(sw, torch, stream, args):
+    """Poisson arrivals into sw_server; latency = submit to poll."""
+    m = args.serve_requests
+    rng_seed = 0xC5
+    arr = gen.splitmix64_block(rng_seed, 0, m)
+    u = (arr >> np.uint64(11)).astype(np.float64) / float(1 << 53)
+    ds = []
+    for i in range(m):
+        st = gen._Stream(100000 + i)
+        n = 32 + int(gen.below(st.draw(1), 97)[0])
+        k = 2 + int(gen.below(st.draw(1), 3)[0])
+        ds.append(gen.random_automaton(n, k, 200000 + i))
+    hs = [sw.load(d) for d in ds]
+    ws = sw.workspace(16 << 30)
+    # capacity: the same requests as one batch
+    sw.sw_batch(hs[:64], ws=ws, word_cap=4096)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    sw.sw_batch(hs, ws=ws, word_cap=4096)
+    torch.cuda.synchronize()
+    cap = m / (time.perf_counter() - t0)
+    lam = 0.8 * cap
+    gaps = -np.log(1.0 - u) / lam
+    del ws
+    srv = sw.Server(sw.workspace(16 << 30), n_max=128, k_max=4, max_requests=m, word_cap=4096)
+    sub_t = np.zeros(m)
+    lat = np.zeros(m)
+    got = 0
+    t_start = time.perf_counter()
+    next_t = t_start
+    i = 0
+    while got < m:
+        now = time.perf_counter()
+        while i < m and now >= next_t:
+            if srv.submit(hs[i], i) != 0:
+                break
+            sub_t[i] = time.perf_counter()
+            next_t += gaps[i]
+            i += 1
+        res = srv.poll()
+        while res is not None:
+            lat[res[0]] = time.perf_counter() - sub_t[res[0]]
+            if res[3] != 0:
+                raise RuntimeError(f"served request {res[0]} failed: {res[3]}")
+            got += 1
+            res = srv.poll()
+        if time.perf_counter() - t_start > 120:
+            raise RuntimeError("serving run exceeded 120 s")
+        time.sleep(0.0002)
+    total = time.perf_counter() - t_start
+    srv.close()
+    return {"requests": m, "arrivals": "Poisson, SplitMix64 seed 0xC5", "lambda_per_s": lam,
+            "batched_capacity_per_s": cap, "instances_per_s": m / total,
+            "p50_ms": float(np.percentile(lat, 50) * 1e3), "p99_ms": float(np.percentile(lat, 99) * 1e3),
+            "workload": "random automata n~U[32,128], k~U{2,3,4}"}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -194,6 +257,8 @@ def main():
     ap.add_argument("--one-sample", type=int, default=256)
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--count", type=int, default=0, help="use only the first COUNT instances (small cases)")
+    ap.add_argument("--no-serve", action="store_true")
+    ap.add_argument("--serve-requests", type=int, default=1500)
     args = ap.parse_args()
 
     rank = int(os.environ.get("RANK", "0"))
@@ -328,24 +393,34 @@ def main():
     st = stats[-1]
     meet_ms = sum(s["meet_ms"] for s in stats) / len(stats)
     pairs = sum(s["pairs"] for s in stats) / len(stats)
+    iters = sum(s["and_iters"] for s in stats) / len(stats)
+    rows_t = sum(s["rows_transposed"] for s in stats) / len(stats)
     launches = sum(s["meet_launches"] for s in stats) / len(stats)
-    ops = pairs * 2 * W
-    achieved = ops / (meet_ms * 1e-3) / 1e12 if meet_ms > 0 else 0.0
+    ops = iters * 64 + rows_t * 2 * W * 25
+    smem_bytes = iters * 256 + rows_t * 8 * W
+    sec = meet_ms * 1e-3
+    achieved = ops / sec / 1e12 if sec > 0 else 0.0
     props = torch.cuda.get_device_properties(local)
     clocks = clk.summary()
-    peak = INT32_LANES_PER_SM * props.multi_processor_count * SM_MAX_MHZ_FALLBACK * 1e6 / 1e12
+    nsm = props.multi_processor_count
+    peak = INT32_LANES_PER_SM * nsm * SM_MAX_MHZ_FALLBACK * 1e6 / 1e12
+    smem_peak = SMEM_BYTES_PER_CLK_SM * nsm * SM_MAX_MHZ_FALLBACK * 1e6 / 1e12
+    serving = serve_bench(sw, torch, stream, args) if rank == 0 and not args.no_serve else None
     line = {
         "metric": "exact-r instances/sec", "value": value, "unit": "instances/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic", "config": cfg,
         "e2e": {"value": count * world / e2e_s, "unit": "instances/s", "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h},
-        "roofline": {"bound": "alu", "kernel": "k_meet", "achieved": achieved, "peak": peak, "unit": "Tops/s",
+        "roofline": {"bound": "alu", "kernel": "k_meet_bm", "achieved": achieved, "peak": peak, "unit": "Tops/s",
                      "frac": achieved / peak if peak else None, "traffic": None,
-                     "ops_per_pair": 2 * W, "pairs_per_step": pairs, "launches_per_step": launches,
-                     "avg_launch_ms": meet_ms / max(launches, 1),
-                     "peak_basis": f"{INT32_LANES_PER_SM} int32 lanes/SM x {props.multi_processor_count} SMs x "
-                                   f"{SM_MAX_MHZ_FALLBACK:.0f} MHz"},
+                     "work": "int32 ops executed: 64 per warp AND step + 25 per transposed 32-bit row word",
+                     "and_steps_per_step": iters, "rows_transposed_per_step": rows_t,
+                     "smem_tbs": smem_bytes / sec / 1e12 if sec > 0 else 0.0, "smem_peak_tbs": smem_peak,
+                     "pairs_per_step": pairs, "pairs_per_sec_in_kernel": pairs / sec if sec > 0 else 0.0,
+                     "launches_per_step": launches, "avg_launch_ms": meet_ms / max(launches, 1),
+                     "peak_basis": f"{INT32_LANES_PER_SM} int32 lanes/SM x {nsm} SMs x "
+                                   f"{SM_MAX_MHZ_FALLBACK:.0f} MHz (max SM clock)"},
         "subset_checks_per_sec": pairs / (ms * 1e-3),
         "kernel_ms_per_step": {"meet": meet_ms, "expand": sum(s["expand_ms"] for s in stats) / len(stats),
                                "compact": sum(s["compact_ms"] for s in stats) / len(stats)},
@@ -353,6 +428,7 @@ def main():
         "arena_peak_sets": st["arena_peak"],
         "one_at_a_time": {"value": m / one_s, "unit": "instances/s", "sample": f"first {m} instances",
                           "batched_same_sample": m / batch_m_s},
+        "serving": serving,
         "clocks": clocks,
         "gpu_launches": int(st.get("launches", 0)),
         "cpu_baseline": cpu,

@@ -166,11 +166,14 @@ int32_t sw_batch_device(int32_t count, const int32_t *n, const int32_t *k,
  *   arena_peak:   most sets stored at once (all instances of a wave).
  *   and_iters:    warp-wide AND steps of the bitmap meet kernel (each ANDs
  *                 one 2048-bit state bitmap into the running intersection).
+ *   rows_transposed: backward sets transposed into per-state bitmaps by the
+ *                 bitmap meet kernel (once per tile).
  */
 int32_t sw_last_stats(int64_t *pairs, int64_t *candidates, int32_t *iterations,
                       double *meet_ms, double *expand_ms, double *compact_ms,
                       int32_t *meet_launches, int64_t *launches, int32_t *waves,
-                      int32_t *evictions, int64_t *arena_peak, int64_t *and_iters);
+                      int32_t *evictions, int64_t *arena_peak, int64_t *and_iters,
+                      int64_t *rows_transposed);
 
 /* Enables (1) or disables (0) per-kernel CUDA-event timing for later
  * searches on the calling thread. */
@@ -187,7 +190,7 @@ void sw_set_timing(int32_t on);
  *                         registers (1, 2, 4 or 8; 0 = pick by word count).
  *   meet_b_tile:          direct test: backward sets per shared-memory tile
  *                         (even).
- *   meet_f_rows:          bitmap test: forward sets per tile (0 = 2048).
+ *   meet_f_rows:          bitmap test: forward sets per tile (0 = 4096).
  *   dir_theta:            a forward step is taken when its predicted cost is
  *                         at most dir_theta times the backward step's.
  *   set_cost:             cost of producing one set, in pair tests (the
@@ -205,6 +208,40 @@ typedef struct sw_options {
 
 void sw_get_options(sw_options *opt);
 void sw_set_options(const sw_options *opt);
+
+/*
+ * Serving: continuous batching of searches (Section 2.1 per request, as
+ * sw_reset_threshold).  A worker thread owns `stream` and the workspace
+ * (caller-owned device memory, kept alive until sw_server_destroy).
+ * Requests submitted while others are running join the running iterations:
+ * between two iterations the worker admits waiting requests while the set
+ * and table pools of the workspace are below half full, and every admitted
+ * request advances one level per iteration in the same kernel launches as
+ * the others.  Each search's levels and tables stay on the device until it
+ * finishes; its result then goes to a completion queue.
+ *
+ * sw_server_create: n_max, k_max bound the automata that may be submitted;
+ *   max_requests bounds requests held at once (queued + running + finished
+ *   but not yet polled); word_cap is the longest word kept per request.
+ * sw_server_submit: copies the automaton of h (h may be freed afterwards);
+ *   non-blocking; SW_EBUSY when max_requests submissions are waiting.
+ * sw_server_poll: non-blocking; SW_EAGAIN when no request has finished.
+ *   On SW_OK: *req_id, *r (-1 if the search failed), *code (the request's
+ *   own status: SW_OK, SW_ENOMEM, SW_EWORDCAP, ...), and when word is not
+ *   NULL and *code is SW_OK the r letters of the least reset word.
+ * sw_server_pending: counts of queued, running and finished-but-unpolled
+ *   requests; returns SW_OK or the worker's fatal error (SW_ECUDA ...).
+ * sw_server_destroy: stops the worker after its current iteration.
+ */
+typedef struct sw_server sw_server;
+
+int32_t sw_server_create(void *workspace, size_t ws_bytes, int32_t n_max, int32_t k_max,
+                         int32_t max_requests, int32_t word_cap, void *stream, sw_server **srv);
+int32_t sw_server_submit(sw_server *srv, sw_handle h, uint64_t req_id);
+int32_t sw_server_poll(sw_server *srv, uint64_t *req_id, int32_t *r, uint8_t *word,
+                       int32_t word_cap, int32_t *code);
+int32_t sw_server_pending(sw_server *srv, int32_t *queued, int32_t *active, int32_t *finished);
+void sw_server_destroy(sw_server *srv);
 
 #ifdef __cplusplus
 }

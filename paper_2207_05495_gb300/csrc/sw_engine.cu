@@ -10,10 +10,18 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <atomic>
+#include <chrono>
+#include <condition_variable>
+#include <mutex>
+#include <thread>
 #include <cmath>
 #include <cstdint>
 #include <cstring>
 #include <deque>
+#include <map>
+#include <memory>
+#include <set>
 #include <new>
 #include <vector>
 
@@ -37,13 +45,14 @@ struct Stats {
     double meet_ms = 0, expand_ms = 0, compact_ms = 0;
     int32_t meet_launches = 0;
     int64_t and_iters = 0;  // bitmap meet: warp-wide AND steps
+    int64_t rows_transposed = 0;  // bitmap meet: backward rows transposed into shared memory
     int64_t launches = 0;  // every kernel launch of the search
     int32_t waves = 0, evictions = 0;
     int64_t arena_peak = 0;  // most sets stored at once
 };
 
 thread_local int32_t g_last_error = SW_OK;
-thread_local sw_options g_opt = {0, 0, 0, 0, 1.0, 16384.0};
+thread_local sw_options g_opt = {0, 0, 0, 4096, 1.0, 8192.0};
 thread_local bool g_timing = false;
 thread_local Stats g_stats;
 
@@ -118,51 +127,116 @@ struct Pinned {
 };
 thread_local Pinned g_up, g_down, g_words;
 
+// ---------------------------------------------------------------- pool allocator
+
+// Best-fit allocator over an index range [0, cap) of device slots (sets or
+// table slots), kept on the host; freed ranges are coalesced.
+struct Pool {
+    int64_t cap = 0, used = 0;
+    std::map<int64_t, int64_t> by_off;                 // free: offset -> length
+    std::set<std::pair<int64_t, int64_t>> by_len;      // free: (length, offset)
+    void init(int64_t c) {
+        cap = c;
+        used = 0;
+        by_off.clear();
+        by_len.clear();
+        if (c > 0) {
+            by_off[0] = c;
+            by_len.insert({c, 0});
+        }
+    }
+    int64_t alloc(int64_t n) {
+        if (n < 1) n = 1;
+        auto it = by_len.lower_bound({n, INT64_MIN});
+        if (it == by_len.end()) return -1;
+        int64_t len = it->first, off = it->second;
+        by_len.erase(it);
+        by_off.erase(off);
+        if (len > n) {
+            by_off[off + n] = len - n;
+            by_len.insert({len - n, off + n});
+        }
+        used += n;
+        return off;
+    }
+    void release(int64_t off, int64_t n) {
+        if (n < 1 || off < 0) return;
+        used -= n;
+        auto next = by_off.lower_bound(off);
+        if (next != by_off.end() && next->first == off + n) {
+            n += next->second;
+            by_len.erase({next->second, next->first});
+            next = by_off.erase(next);
+        }
+        if (next != by_off.begin()) {
+            auto prev = std::prev(next);
+            if (prev->first + prev->second == off) {
+                off = prev->first;
+                n += prev->second;
+                by_len.erase({prev->second, prev->first});
+                by_off.erase(prev);
+            }
+        }
+        by_off[off] = n;
+        by_len.insert({n, off});
+    }
+};
+
 // ---------------------------------------------------------------- per-instance state
 
 enum InstState { kWaiting = 0, kActive = 1, kDone = 2, kFailed = 3 };
 
+struct Level {
+    int64_t off, cnt, cap;  // arena index, sets, slots held in the set pool
+};
+
 struct Inst {
     int32_t n = 0, k = 0, orig = 0;
     int64_t delta_off = 0;
-    std::vector<int64_t> off[2], cnt[2];
+    std::vector<Level> lev[2];
+    int64_t tab_off[2] = {-1, -1}, tab_cap[2] = {0, 0}, stored[2] = {0, 0};
     double dupl[2] = {0.0, 0.0};
     int32_t state = kWaiting, code = SW_OK, r = -1;
     int32_t evictions = 0;
-    int64_t stored = 0;
-    // where the word goes
-    int64_t word_off = 0, word_cap = 0;
+    int64_t word_off = 0, word_cap = 0;    // where the word goes
+    std::vector<int64_t> sizes[2];         // level sizes of the finished search
+    int64_t footprint() const {
+        int64_t b = 0;
+        for (int d = 0; d < 2; ++d) {
+            for (auto &l : lev[d]) b += l.cap;
+            b += tab_cap[d] / 4;  // a table slot is a quarter of a set (W = 1) or less
+        }
+        return b;
+    }
 };
 
+// ---------------------------------------------------------------- workspace layout
+
 struct Layout {
-    // small per-iteration areas
-    ExpandJob *jobs;
-    MeetJob *mjobs;
-    RootJob *rjobs;
-    WordJob *wjobs;
-    int64_t *blevels;
-    int64_t blevels_cap;
-    uint64_t *job_rank;     // njobs + 1
+    // staging mirror for per-iteration job uploads (one H2D copy per phase)
+    char *mirror;
+    size_t mirror_bytes;
+    uint64_t *counts;  // per-job survivors
     unsigned long long *best;
     uint32_t *word_status;
     uint32_t *status;
-    unsigned long long *pairs;  // [0] pairs tested, [1] bitmap AND steps
+    unsigned long long *pairs;  // [0] pairs tested, [1] bitmap AND steps, [2] rows transposed
     uint8_t *word_area;
     int64_t word_area_cap;
     uint16_t *delta16;
-    // big areas
+    int64_t delta_cap;
+    // pools
     uint64_t *sets, *link;
-    uint32_t *owner;
     int64_t cap_sets;
+    uint64_t *table;
+    int64_t cap_table;
+    // candidates of the running expansion
     uint64_t *cand_sets;
-    uint32_t *cand_owner;
     int64_t *cand_slot;
     uint8_t *flag;
     uint32_t *block_cnt;
     uint64_t *block_off;
     int64_t cap_cand;
-    uint64_t *table;
-    uint64_t cap_table;
 };
 
 struct Carver {
@@ -183,77 +257,87 @@ struct Carver {
     }
 };
 
+size_t mirror_bytes_for(int32_t count) { return (size_t)std::max(count, 1) * 1024 + (1 << 20); }
+int64_t word_area_for(int32_t count) { return (int64_t)std::max<size_t>((size_t)std::max(count, 1) * 512, 1 << 20); }
+
 size_t small_area_bytes(int32_t count, int64_t delta_elems) {
     size_t c = (size_t)std::max(count, 1);
     size_t b = 0;
     auto add = [&](size_t x) { b += (x + 255) & ~(size_t)255; };
-    add(c * sizeof(ExpandJob));
-    add(c * sizeof(MeetJob));
-    add(c * sizeof(RootJob));
-    add(c * sizeof(WordJob));
-    add((c * 256 + 4096) * 2 * sizeof(int64_t));  // blevels
-    add((c + 1) * sizeof(uint64_t));
+    add(mirror_bytes_for(count));
+    add(c * sizeof(uint64_t));
     add(c * sizeof(unsigned long long));
     add(c * sizeof(uint32_t));
     add(sizeof(uint32_t));
-    add(2 * sizeof(unsigned long long));
-    add(std::max<size_t>(c * 512, 1 << 20));  // word area
-    add((size_t)delta_elems * sizeof(uint16_t));
+    add(3 * sizeof(unsigned long long));
+    add((size_t)word_area_for(count));
+    add((size_t)std::max<int64_t>(delta_elems, 1) * sizeof(uint16_t));
     return b;
 }
 
-bool carve(void *ws, size_t bytes, int W, int32_t count, int64_t delta_elems, int kmax, Layout &L) {
+// Splits the workspace: small areas, then the set pool (set + link), the
+// table pool and the candidate buffers, in proportions for W words.
+bool carve(void *ws, size_t bytes, int W, int32_t count, int64_t delta_elems, Layout &L) {
     Carver cv(ws, bytes);
     size_t c = (size_t)std::max(count, 1);
-    L.jobs = cv.take<ExpandJob>(c);
-    L.mjobs = cv.take<MeetJob>(c);
-    L.rjobs = cv.take<RootJob>(c);
-    L.wjobs = cv.take<WordJob>(c);
-    L.blevels_cap = (int64_t)(c * 256 + 4096);
-    L.blevels = cv.take<int64_t>((size_t)L.blevels_cap * 2);
-    L.job_rank = cv.take<uint64_t>(c + 1);
+    L.mirror_bytes = mirror_bytes_for(count);
+    L.mirror = cv.take<char>(L.mirror_bytes);
+    L.counts = cv.take<uint64_t>(c);
     L.best = cv.take<unsigned long long>(c);
     L.word_status = cv.take<uint32_t>(c);
     L.status = cv.take<uint32_t>(1);
-    L.pairs = cv.take<unsigned long long>(2);
-    L.word_area_cap = (int64_t)std::max<size_t>(c * 512, 1 << 20);
+    L.pairs = cv.take<unsigned long long>(3);
+    L.word_area_cap = word_area_for(count);
     L.word_area = cv.take<uint8_t>((size_t)L.word_area_cap);
-    L.delta16 = cv.take<uint16_t>((size_t)std::max<int64_t>(delta_elems, 1));
+    L.delta_cap = std::max<int64_t>(delta_elems, 1);
+    L.delta16 = cv.take<uint16_t>((size_t)L.delta_cap);
     if (!cv.ok) return false;
-    // The rest: stored sets (set + link + owner), candidates (set + owner +
-    // slot + flag + block counts), and the table with two slots per set that
-    // can be present at once (stored + candidates), i.e. load <= 1/2.
-    double rho = kmax > 2 ? 1.0 : 0.5;  // candidate capacity relative to stored capacity
-    double per_set = (8.0 * W + 12) + rho * (8.0 * W + 8 + 4 + 1 + 4.0 / kScanBlock + 8.0 / kScanBlock) +
-                     16.0 * (1 + rho);
     size_t rest = cv.size - cv.used;
-    if (rest < 64 * 1024) return false;
-    int64_t S = (int64_t)((double)(rest - 16 * 1024) / per_set);
-    for (;; S = S * 15 / 16) {
-        if (S < 64) return false;
-        Carver t = cv;
-        int64_t C = std::max<int64_t>((int64_t)(S * rho), 64);
-        C = std::min<int64_t>(C, (int64_t)0xF0000000);
-        int64_t nblocks = (C + kScanBlock - 1) / kScanBlock;
-        uint64_t T = (uint64_t)(2 * (S + C));
-        L.sets = t.take<uint64_t>((size_t)S * W);
-        L.link = t.take<uint64_t>((size_t)S);
-        L.owner = t.take<uint32_t>((size_t)S);
-        L.cand_sets = t.take<uint64_t>((size_t)C * W);
-        L.cand_owner = t.take<uint32_t>((size_t)C);
-        L.cand_slot = t.take<int64_t>((size_t)C);
-        L.flag = t.take<uint8_t>((size_t)C);
-        L.block_cnt = t.take<uint32_t>((size_t)nblocks);
-        L.block_off = t.take<uint64_t>((size_t)nblocks + 1);
-        L.table = t.take<uint64_t>((size_t)T);
-        if (t.ok) {
-            L.cap_sets = S;
-            L.cap_cand = C;
-            L.cap_table = T;
-            return true;
-        }
-    }
+    if (rest < 256 * 1024) return false;
+    rest -= 16 * 1024;
+    // bytes: sets 55%, table 25%, candidates 20%
+    double set_b = 8.0 * W + 8, cand_b = 8.0 * W + 8 + 1 + 12.0 / kScanBlock;
+    int64_t S = (int64_t)(0.55 * rest / set_b);
+    int64_t T = (int64_t)(0.25 * rest / 8.0);
+    int64_t C = (int64_t)(0.20 * rest / cand_b);
+    C = std::min<int64_t>(C, (int64_t)0xF0000000) / kScanBlock * kScanBlock;
+    if (S < 64 || T < 256 || C < kScanBlock) return false;
+    int64_t nblocks = C / kScanBlock;
+    L.sets = cv.take<uint64_t>((size_t)S * W);
+    L.link = cv.take<uint64_t>((size_t)S);
+    L.table = cv.take<uint64_t>((size_t)T);
+    L.cand_sets = cv.take<uint64_t>((size_t)C * W);
+    L.cand_slot = cv.take<int64_t>((size_t)C);
+    L.flag = cv.take<uint8_t>((size_t)C);
+    L.block_cnt = cv.take<uint32_t>((size_t)nblocks);
+    L.block_off = cv.take<uint64_t>((size_t)nblocks + 1);
+    if (!cv.ok) return false;
+    L.cap_sets = S;
+    L.cap_table = T;
+    L.cap_cand = C;
+    return true;
 }
+
+// Packs several job arrays into the pinned staging buffer and the device
+// mirror so that one H2D copy moves them all.
+struct Staging {
+    char *host = nullptr, *dev = nullptr;
+    size_t cap = 0, used = 0;
+    bool ok = true;
+    template <class T>
+    T *take(size_t count, T **dev_ptr) {
+        size_t bytes = (count * sizeof(T) + 255) & ~(size_t)255;
+        if (used + bytes > cap) {
+            ok = false;
+            return nullptr;
+        }
+        T *h = (T *)(host + used);
+        *dev_ptr = (T *)(dev + used);
+        used += bytes;
+        return h;
+    }
+    bool fits(size_t more) const { return used + more + 256 * 8 <= cap; }
+};
 
 // ---------------------------------------------------------------- kernel dispatch
 
@@ -272,7 +356,7 @@ int default_rows(int W) { return W == 1 ? 8 : (W <= 3 ? 4 : 2); }
 int default_btile(int W) { return std::max(64, (4096 / W) & ~1); }
 
 struct MeetCfg {
-    int algo;  // 0 vertical bitmaps, 1 direct LOP3 test
+    int algo;     // 0 vertical bitmaps, 1 direct LOP3 test
     int R, tb, nt;
     int tf_rows;  // forward rows per tile (bitmap kernel)
 };
@@ -291,7 +375,7 @@ MeetCfg meet_cfg(int W) {
     c.nt = 256;
     c.algo = g_opt.meet_algo == 1 ? 1 : 0;
     if (c.algo == 0) c.tb = kBmRows;
-    c.tf_rows = g_opt.meet_f_rows > 0 ? g_opt.meet_f_rows : 2048;
+    c.tf_rows = g_opt.meet_f_rows > 0 ? g_opt.meet_f_rows : 4096;
     c.tf_rows = std::max(8, std::min(c.tf_rows, 1 << 20));
     return c;
 }
@@ -319,7 +403,7 @@ cudaError_t launch_meet_r(const MeetJob *jobs, int njobs, int64_t ntiles, int tb
 template <int W>
 cudaError_t launch_meet_bm(const MeetJob *jobs, int njobs, int64_t ntiles, int tf_rows, const uint64_t *sets,
                            unsigned long long *best, unsigned long long *pairs, unsigned long long *iters,
-                           cudaStream_t st) {
+                           unsigned long long *rows, cudaStream_t st) {
     constexpr int NT = 256;
     auto kern = k_meet_bm<W, NT>;
     size_t smem = (size_t)64 * W * kBmStride * sizeof(uint32_t);
@@ -332,71 +416,92 @@ cudaError_t launch_meet_bm(const MeetJob *jobs, int njobs, int64_t ntiles, int t
     int per_sm = 0;
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, NT, smem);
     int64_t grid = std::min<int64_t>((int64_t)sm_count() * std::max(per_sm, 1), ntiles);
-    kern<<<(unsigned)grid, NT, smem, st>>>(jobs, njobs, ntiles, tf_rows, sets, best, pairs, iters);
+    kern<<<(unsigned)grid, NT, smem, st>>>(jobs, njobs, ntiles, tf_rows, sets, best, pairs, iters, rows);
     return cudaGetLastError();
 }
 
 template <int W>
 struct Ops {
-    static cudaError_t roots(const RootJob *j, int nj, int nmax, const Layout &L, cudaStream_t st) {
-        dim3 grid((unsigned)((nmax + 1 + 255) / 256), (unsigned)nj);
-        g_stats.launches++;
-        k_roots<W><<<grid, 256, 0, st>>>(j, nj, L.sets, L.link, L.owner, L.table, L.cap_table, L.status);
+    static cudaError_t fill(const FillJob *j, int nj, int64_t maxlen, const Layout &L, cudaStream_t st) {
+        for (int b = 0; b < nj; b += 65535) {
+            dim3 grid((unsigned)std::min<int64_t>((maxlen + 255) / 256, 256), (unsigned)std::min(65535, nj - b));
+            g_stats.launches++;
+            k_fill<<<grid, 256, 0, st>>>(j + b, L.table);
+        }
         return cudaGetLastError();
     }
-    static cudaError_t expand(int nj, int64_t ncand, const Layout &L, cudaStream_t st) {
+    static cudaError_t roots(const RootJob *j, int nj, int nmax, const Layout &L, cudaStream_t st) {
+        for (int b = 0; b < nj; b += 65535) {
+            dim3 grid((unsigned)((nmax + 1 + 255) / 256), (unsigned)std::min(65535, nj - b));
+            g_stats.launches++;
+            k_roots<W><<<grid, 256, 0, st>>>(j + b, L.sets, L.link, L.table, L.status);
+        }
+        return cudaGetLastError();
+    }
+    static cudaError_t rehash(const RehashSeg *segs, int nseg, int64_t total, const Layout &L, cudaStream_t st) {
+        int64_t blocks = std::min<int64_t>((total + 255) / 256, (int64_t)sm_count() * 16);
+        g_stats.launches++;
+        k_rehash<W><<<(unsigned)std::max<int64_t>(blocks, 1), 256, 0, st>>>(segs, nseg, total, L.sets, L.table,
+                                                                             L.status);
+        return cudaGetLastError();
+    }
+    static cudaError_t expand(const ExpandJob *jobs, int nj, int64_t ncand, const Layout &L, cudaStream_t st) {
         int64_t blocks = std::min<int64_t>((ncand + 255) / 256, (int64_t)sm_count() * 16);
         g_stats.launches++;
         k_expand<W><<<(unsigned)std::max<int64_t>(blocks, 1), 256, 0, st>>>(
-            L.jobs, nj, ncand, L.delta16, L.sets, L.owner, L.table, L.cap_table, L.cand_sets, L.cand_owner,
-            L.cand_slot, L.status);
+            jobs, nj, ncand, L.delta16, L.sets, L.table, L.cand_sets, L.cand_slot, L.status);
         return cudaGetLastError();
     }
-    static cudaError_t compact(int nj, int64_t ncand, int64_t top, const Layout &L, cudaStream_t st) {
-        int64_t nblocks = (ncand + kScanBlock - 1) / kScanBlock;
-        g_stats.launches += 3;
+    static cudaError_t compact(const ExpandJob *jobs, int nj, int64_t ncand, const Layout &L, cudaStream_t st) {
+        int64_t nblocks = ncand / kScanBlock;
+        g_stats.launches += 4;
         k_flag_count<<<(unsigned)nblocks, kScanThreads, 0, st>>>(ncand, L.cand_slot, L.table, L.flag, L.block_cnt);
         k_scan_blocks<<<1, 1024, 0, st>>>(nblocks, L.block_cnt, L.block_off);
-        k_compact<W><<<(unsigned)nblocks, kScanThreads, 0, st>>>(L.jobs, nj, ncand, L.flag, L.block_off, L.cand_sets,
-                                                                 L.cand_owner, L.cand_slot, L.table, top, L.sets,
-                                                                 L.link, L.owner, L.job_rank);
+        k_compact<W><<<(unsigned)nblocks, kScanThreads, 0, st>>>(jobs, nj, ncand, L.flag, L.block_off, L.cand_sets,
+                                                                 L.cand_slot, L.table, L.sets, L.link);
+        k_job_counts<<<(unsigned)((nj + 255) / 256), 256, 0, st>>>(jobs, nj, nblocks, L.block_off, L.counts);
         return cudaGetLastError();
     }
-    static cudaError_t meet(int nj, int64_t ntiles, const MeetCfg &c, const Layout &L, cudaStream_t st) {
+    static cudaError_t meet(const MeetJob *jobs, int nj, int64_t ntiles, const MeetCfg &c, const Layout &L,
+                            cudaStream_t st) {
         g_stats.launches++;
         if (c.algo == 0)
-            return launch_meet_bm<W>(L.mjobs, nj, ntiles, c.tf_rows, L.sets, L.best, L.pairs, L.pairs + 1, st);
+            return launch_meet_bm<W>(jobs, nj, ntiles, c.tf_rows, L.sets, L.best, L.pairs, L.pairs + 1, L.pairs + 2,
+                                     st);
         switch (c.R) {
             case 1:
-                if constexpr (W >= 3) return launch_meet_r<W, 1>(L.mjobs, nj, ntiles, c.tb, L.sets, L.best, L.pairs, st);
+                if constexpr (W >= 3) return launch_meet_r<W, 1>(jobs, nj, ntiles, c.tb, L.sets, L.best, L.pairs, st);
                 break;
-            case 2: return launch_meet_r<W, 2>(L.mjobs, nj, ntiles, c.tb, L.sets, L.best, L.pairs, st);
-            case 4: return launch_meet_r<W, 4>(L.mjobs, nj, ntiles, c.tb, L.sets, L.best, L.pairs, st);
+            case 2: return launch_meet_r<W, 2>(jobs, nj, ntiles, c.tb, L.sets, L.best, L.pairs, st);
+            case 4: return launch_meet_r<W, 4>(jobs, nj, ntiles, c.tb, L.sets, L.best, L.pairs, st);
             case 8:
-                if constexpr (W <= 2) return launch_meet_r<W, 8>(L.mjobs, nj, ntiles, c.tb, L.sets, L.best, L.pairs, st);
+                if constexpr (W <= 2) return launch_meet_r<W, 8>(jobs, nj, ntiles, c.tb, L.sets, L.best, L.pairs, st);
                 break;
         }
         return cudaErrorInvalidValue;
     }
-    static cudaError_t words(int nj, uint8_t *base, const Layout &L, cudaStream_t st) {
+    static cudaError_t words(const WordJob *jobs, const int64_t *blevels, int nj, uint8_t *base, const Layout &L,
+                             cudaStream_t st) {
         g_stats.launches++;
-        k_words<W, 256><<<(unsigned)nj, 256, 0, st>>>(L.wjobs, L.blevels, L.delta16, L.sets, L.link, base,
-                                                       L.word_status);
+        k_words<W, 256><<<(unsigned)nj, 256, 0, st>>>(jobs, blevels, L.delta16, L.sets, L.link, base, L.word_status);
         return cudaGetLastError();
     }
 };
 
 struct OpTable {
+    cudaError_t (*fill)(const FillJob *, int, int64_t, const Layout &, cudaStream_t);
     cudaError_t (*roots)(const RootJob *, int, int, const Layout &, cudaStream_t);
-    cudaError_t (*expand)(int, int64_t, const Layout &, cudaStream_t);
-    cudaError_t (*compact)(int, int64_t, int64_t, const Layout &, cudaStream_t);
-    cudaError_t (*meet)(int, int64_t, const MeetCfg &, const Layout &, cudaStream_t);
-    cudaError_t (*words)(int, uint8_t *, const Layout &, cudaStream_t);
+    cudaError_t (*rehash)(const RehashSeg *, int, int64_t, const Layout &, cudaStream_t);
+    cudaError_t (*expand)(const ExpandJob *, int, int64_t, const Layout &, cudaStream_t);
+    cudaError_t (*compact)(const ExpandJob *, int, int64_t, const Layout &, cudaStream_t);
+    cudaError_t (*meet)(const MeetJob *, int, int64_t, const MeetCfg &, const Layout &, cudaStream_t);
+    cudaError_t (*words)(const WordJob *, const int64_t *, int, uint8_t *, const Layout &, cudaStream_t);
 };
 
 template <int W>
 OpTable make_ops() {
-    return {&Ops<W>::roots, &Ops<W>::expand, &Ops<W>::compact, &Ops<W>::meet, &Ops<W>::words};
+    return {&Ops<W>::fill, &Ops<W>::roots, &Ops<W>::rehash, &Ops<W>::expand, &Ops<W>::compact, &Ops<W>::meet,
+            &Ops<W>::words};
 }
 
 OpTable ops_for(int W) {
@@ -437,247 +542,363 @@ float elapsed(cudaEvent_t a, cudaEvent_t b) {
     return ms;
 }
 
-#define CK(x)                                  \
-    do {                                       \
-        cudaError_t e_ = (x);                  \
+#define CK(x)                                   \
+    do {                                        \
+        cudaError_t e_ = (x);                   \
         if (e_ != cudaSuccess) return SW_ECUDA; \
     } while (0)
 
-// ---------------------------------------------------------------- the search
+int64_t round_up(int64_t x, int64_t m) { return (x + m - 1) / m * m; }
 
-struct Search {
+// ---------------------------------------------------------------- the search engine
+
+// Runs instances (state kWaiting, in `queue`) to completion.  Memory of an
+// instance is released as soon as it finishes; when nothing can advance for
+// lack of room, the instance holding the most memory is set back (its
+// memory freed) and rerun after the current active set has drained.
+struct Engine {
     int W;
     cudaStream_t st;
     Layout L;
     OpTable ops;
     MeetCfg mc;
+    Pool set_pool, tab_pool;
     std::vector<Inst> &I;
-    bool device_words;   // words go straight to the caller's device buffer
-    uint8_t *out_words;  // caller's buffer (device when device_words, else host)
-    int64_t top = 0, stored_total = 0;
+    bool device_words = false;  // words go straight to the caller's device buffer
+    uint8_t *out_words = nullptr;
+    Staging stg;
+    std::vector<int> active, deferred;
 
-    Search(int W_, cudaStream_t s, std::vector<Inst> &insts) : W(W_), st(s), I(insts) {
+    Engine(int W_, cudaStream_t s, std::vector<Inst> &insts, const Layout &lay) : W(W_), st(s), L(lay), I(insts) {
         ops = ops_for(W);
         mc = meet_cfg(W);
+        set_pool.init(L.cap_sets);
+        tab_pool.init(L.cap_table);
     }
 
-    int64_t top_peak() const { return top; }
+    bool stage_begin() {
+        stg.host = (char *)g_up.get(L.mirror_bytes);
+        stg.dev = L.mirror;
+        stg.cap = L.mirror_bytes;
+        stg.used = 0;
+        stg.ok = stg.host != nullptr;
+        return stg.ok;
+    }
+    int stage_flush() {
+        if (!stg.ok) return SW_ECUDA;
+        if (stg.used) CK(cudaMemcpyAsync(stg.dev, stg.host, stg.used, cudaMemcpyHostToDevice, st));
+        return SW_OK;
+    }
 
     int choose_dir(const Inst &x) const {
-        double F = (double)x.cnt[0].back(), B = (double)x.cnt[1].back(), k = x.k;
+        double F = (double)x.lev[0].back().cnt, B = (double)x.lev[1].back().cnt, k = x.k;
         double cF = g_opt.set_cost * k * F + k * (1.0 - x.dupl[0]) * F * B;
         double cB = g_opt.set_cost * k * B + k * (1.0 - x.dupl[1]) * B * F;
         return cF <= g_opt.dir_theta * cB ? 0 : 1;
     }
 
-    // Starts a wave: clears the table and stores the roots of `wave`.
-    int start_wave(const std::vector<int> &wave) {
-        g_stats.waves++;
-        top = 0;
-        stored_total = 0;
-        CK(cudaMemsetAsync(L.table, 0xFF, L.cap_table * sizeof(uint64_t), st));
-        CK(cudaMemsetAsync(L.status, 0, sizeof(uint32_t), st));
-        RootJob *rj = (RootJob *)g_up.get(wave.size() * sizeof(RootJob));
-        if (!rj) return SW_ECUDA;
-        int nmax = 1;
-        for (size_t t = 0; t < wave.size(); ++t) {
-            Inst &x = I[wave[t]];
-            if (top + x.n + 1 > L.cap_sets || 2 * (top + x.n + 1) > (int64_t)L.cap_table) return SW_ENOMEM;
-            rj[t] = RootJob{top, (int32_t)wave[t], x.n};
+    void release(Inst &x) {
+        for (int d = 0; d < 2; ++d) {
+            for (auto &l : x.lev[d]) set_pool.release(l.off, l.cap);
+            x.lev[d].clear();
+            if (x.tab_off[d] >= 0) tab_pool.release(x.tab_off[d], x.tab_cap[d]);
+            x.tab_off[d] = -1;
+            x.tab_cap[d] = 0;
+            x.stored[d] = 0;
+        }
+    }
+
+    void finish(Inst &x, int state, int code) {
+        for (int d = 0; d < 2; ++d) {
+            x.sizes[d].clear();
+            for (auto &l : x.lev[d]) x.sizes[d].push_back(l.cnt);
+        }
+        x.state = state;
+        x.code = code;
+        release(x);
+    }
+
+    // Stores the roots of as many of `ids` as fit; returns how many.
+    int admit(const std::vector<int> &ids, size_t first, size_t *taken) {
+        *taken = 0;
+        if (!stage_begin()) return SW_ECUDA;
+        std::vector<int> ok;
+        size_t cap_jobs = (L.mirror_bytes / 2) / (sizeof(RootJob) + 2 * sizeof(FillJob));
+        for (size_t t = first; t < ids.size() && ok.size() < cap_jobs; ++t) {
+            Inst &x = I[ids[t]];
+            int64_t tc0 = 64, tc1 = round_up(4 * (int64_t)x.n, 64);
+            int64_t f = set_pool.alloc(1);
+            int64_t b = f >= 0 ? set_pool.alloc(x.n) : -1;
+            int64_t t0 = b >= 0 ? tab_pool.alloc(tc0) : -1;
+            int64_t t1 = t0 >= 0 ? tab_pool.alloc(tc1) : -1;
+            if (t1 < 0) {
+                if (f >= 0) set_pool.release(f, 1);
+                if (b >= 0) set_pool.release(b, x.n);
+                if (t0 >= 0) tab_pool.release(t0, tc0);
+                break;
+            }
             for (int d = 0; d < 2; ++d) {
-                x.off[d].clear();
-                x.cnt[d].clear();
+                x.lev[d].clear();
                 x.dupl[d] = 0.0;
             }
-            x.off[0].push_back(top);
-            x.cnt[0].push_back(1);
-            x.off[1].push_back(top + 1);
-            x.cnt[1].push_back(x.n);
-            x.stored = x.n + 1;
+            x.lev[0].push_back({f, 1, 1});
+            x.lev[1].push_back({b, x.n, x.n});
+            x.tab_off[0] = t0;
+            x.tab_cap[0] = tc0;
+            x.tab_off[1] = t1;
+            x.tab_cap[1] = tc1;
+            x.stored[0] = 1;
+            x.stored[1] = x.n;
             x.state = kActive;
-            top += x.n + 1;
-            nmax = std::max(nmax, x.n);
+            ok.push_back(ids[t]);
         }
-        stored_total = top;
-        // the kernel reads at most 65535 root jobs per launch (grid.y)
-        CK(cudaMemcpyAsync(L.rjobs, rj, wave.size() * sizeof(RootJob), cudaMemcpyHostToDevice, st));
-        for (size_t b = 0; b < wave.size(); b += 65535)
-            CK(ops.roots(L.rjobs + b, (int)std::min<size_t>(65535, wave.size() - b), nmax, L, st));
+        *taken = ok.size();
+        if (ok.empty()) return SW_OK;
+        int nj = (int)ok.size();
+        RootJob *d_rj;
+        FillJob *d_fj;
+        RootJob *rj = stg.take<RootJob>(nj, &d_rj);
+        FillJob *fj = stg.take<FillJob>(2 * nj, &d_fj);
+        if (!stg.ok) return SW_EINTERNAL;
+        int nmax = 1;
+        int64_t maxlen = 1;
+        for (int t = 0; t < nj; ++t) {
+            Inst &x = I[ok[t]];
+            rj[t] = RootJob{x.lev[0][0].off, x.lev[1][0].off, {x.tab_off[0], x.tab_off[1]},
+                            {x.tab_cap[0], x.tab_cap[1]}, x.n, 0};
+            fj[2 * t] = FillJob{x.tab_off[0], x.tab_cap[0]};
+            fj[2 * t + 1] = FillJob{x.tab_off[1], x.tab_cap[1]};
+            nmax = std::max(nmax, x.n);
+            maxlen = std::max(maxlen, x.tab_cap[1]);
+            active.push_back(ok[t]);
+        }
+        int rc = stage_flush();
+        if (rc) return rc;
+        CK(ops.fill(d_fj, 2 * nj, maxlen, L, st));
+        CK(ops.roots(d_rj, nj, nmax, L, st));
         CK(cudaStreamSynchronize(st));  // the staging buffer is reused next
         return SW_OK;
     }
 
-    // One iteration over the active instances of the wave.  Returns SW_OK,
-    // or a fatal code for the whole wave.
-    int iterate(std::vector<int> &active, std::vector<int> &evicted) {
+    // One iteration over the active instances.
+    int iterate() {
         g_stats.iterations++;
-        // 1. directions and expansion jobs that fit
-        std::vector<int> who;
-        std::vector<int> dirs;
-        ExpandJob *jobs = (ExpandJob *)g_up.get(active.size() * sizeof(ExpandJob));
-        if (!jobs) return SW_ECUDA;
+        if (!stage_begin()) return SW_ECUDA;
+        struct Sel {
+            int id, d;
+            int64_t nc, dest, new_tab, new_cap;
+        };
+        std::vector<Sel> sel;
         int64_t ncand = 0;
+        size_t seg_count = 0;
         for (int id : active) {
             Inst &x = I[id];
             int d = choose_dir(x);
-            int64_t pc = x.cnt[d].back();
+            int64_t pc = x.lev[d].back().cnt;
             int64_t nc = pc * x.k;
-            bool fits = ncand + nc <= L.cap_cand && top + ncand + nc <= L.cap_sets &&
-                        2 * (stored_total + ncand + nc) <= (int64_t)L.cap_table;
-            if (!fits) continue;
-            ExpandJob &J = jobs[who.size()];
-            J.cand_off = ncand;
-            J.parent_off = x.off[d].back();
-            J.parent_cnt = pc;
+            int64_t ncp = round_up(nc, kScanBlock);
+            if (ncand + ncp > L.cap_cand) continue;
+            size_t segs_here = 0;
+            int64_t nt = -1, ntc = 0;
+            if (2 * (x.stored[d] + nc) > x.tab_cap[d]) {  // grow the table: load stays <= 1/2
+                ntc = round_up(3 * (x.stored[d] + nc), 64);
+                segs_here = x.lev[d].size();
+                if (!stg.fits((seg_count + segs_here) * sizeof(RehashSeg) + (sel.size() + 2) * sizeof(ExpandJob) +
+                              (sel.size() + 1) * sizeof(FillJob)))
+                    continue;
+                nt = tab_pool.alloc(ntc);
+                if (nt < 0) continue;
+            }
+            int64_t dest = set_pool.alloc(nc);
+            if (dest < 0) {
+                if (nt >= 0) tab_pool.release(nt, ntc);
+                continue;
+            }
+            if (nt >= 0) {
+                tab_pool.release(x.tab_off[d], x.tab_cap[d]);
+                x.tab_off[d] = nt;
+                x.tab_cap[d] = ntc;
+                seg_count += segs_here;
+            }
+            sel.push_back({id, d, nc, dest, nt, ntc});
+            ncand += ncp;
+        }
+        if (sel.empty()) {
+            // nothing fits: set back the instance holding the most memory
+            auto it = std::max_element(active.begin(), active.end(),
+                                       [&](int a, int b) { return I[a].footprint() < I[b].footprint(); });
+            int id = *it;
+            active.erase(it);
+            Inst &x = I[id];
+            g_stats.evictions++;
+            if (active.empty()) {  // it had all the room there is
+                finish(x, kFailed, SW_ENOMEM);
+            } else {
+                release(x);
+                x.state = kWaiting;
+                x.evictions++;
+                deferred.push_back(id);
+            }
+            return SW_OK;
+        }
+        // jobs, table fills and rehash segments: one upload
+        int nj = (int)sel.size();
+        ExpandJob *d_jobs;
+        ExpandJob *jobs = stg.take<ExpandJob>(nj, &d_jobs);
+        std::vector<FillJob> fills;
+        std::vector<RehashSeg> segs;
+        int64_t cand = 0, rehash_total = 0, maxfill = 1;
+        for (int t = 0; t < nj; ++t) {
+            Sel &s = sel[t];
+            Inst &x = I[s.id];
+            const Level &P = x.lev[s.d].back();
+            ExpandJob &J = jobs[t];
+            J.cand_off = cand;
+            J.parent_off = P.off;
+            J.parent_cnt = P.cnt;
             J.delta_off = x.delta_off;
-            J.owner = (int32_t)(((uint32_t)id << 1) | (uint32_t)d);
+            J.dest_off = s.dest;
+            J.tab_off = x.tab_off[s.d];
+            J.tab_cap = x.tab_cap[s.d];
+            J.dir = s.d;
             J.n = x.n;
             J.k = x.k;
             J.pad = 0;
-            who.push_back(id);
-            dirs.push_back(d);
-            ncand += nc;
+            cand += round_up(s.nc, kScanBlock);
+            if (s.new_tab >= 0) {
+                fills.push_back({s.new_tab, s.new_cap});
+                maxfill = std::max(maxfill, s.new_cap);
+                for (auto &l : x.lev[s.d]) {
+                    segs.push_back({rehash_total, l.off, l.cnt, s.new_tab, s.new_cap, s.d, 0});
+                    rehash_total += l.cnt;
+                }
+            }
         }
-        if (who.empty()) {
-            // nothing fits: give up the instance holding the most sets; it
-            // is retried in a later wave (the wave loop fails it only if it
-            // ran alone)
-            auto it = std::max_element(active.begin(), active.end(),
-                                       [&](int a, int b) { return I[a].stored < I[b].stored; });
-            int id = *it;
-            active.erase(it);
-            I[id].state = kWaiting;
-            I[id].evictions++;
-            g_stats.evictions++;
-            evicted.push_back(id);
-            return SW_OK;
+        FillJob *d_fill = nullptr;
+        RehashSeg *d_segs = nullptr;
+        if (!fills.empty()) {
+            FillJob *f = stg.take<FillJob>(fills.size(), &d_fill);
+            RehashSeg *g = stg.take<RehashSeg>(segs.size(), &d_segs);
+            if (!stg.ok) return SW_EINTERNAL;
+            std::memcpy(f, fills.data(), fills.size() * sizeof(FillJob));
+            std::memcpy(g, segs.data(), segs.size() * sizeof(RehashSeg));
         }
-        int nj = (int)who.size();
+        if (!stg.ok) return SW_EINTERNAL;
+        int rc = stage_flush();
+        if (rc) return rc;
         g_stats.candidates += ncand;
-        CK(cudaMemcpyAsync(L.jobs, jobs, nj * sizeof(ExpandJob), cudaMemcpyHostToDevice, st));
+        if (!fills.empty()) {
+            CK(ops.fill(d_fill, (int)fills.size(), maxfill, L, st));
+            CK(ops.rehash(d_segs, (int)segs.size(), rehash_total, L, st));
+        }
         if (g_timing) CK(cudaEventRecord(g_ev.ev[0], st));
-        CK(ops.expand(nj, ncand, L, st));
+        CK(ops.expand(d_jobs, nj, ncand, L, st));
         if (g_timing) CK(cudaEventRecord(g_ev.ev[1], st));
-        CK(ops.compact(nj, ncand, top, L, st));
+        CK(ops.compact(d_jobs, nj, ncand, L, st));
         if (g_timing) CK(cudaEventRecord(g_ev.ev[2], st));
-        int64_t nblocks = (ncand + kScanBlock - 1) / kScanBlock;
-        // 2. results of the compaction
-        uint64_t *down = (uint64_t *)g_down.get((nj + 2) * sizeof(uint64_t));
+        uint64_t *down = (uint64_t *)g_down.get((nj + 1) * sizeof(uint64_t));
         if (!down) return SW_ECUDA;
-        CK(cudaMemcpyAsync(down, L.job_rank, nj * sizeof(uint64_t), cudaMemcpyDeviceToHost, st));
-        CK(cudaMemcpyAsync(down + nj, L.block_off + nblocks, sizeof(uint64_t), cudaMemcpyDeviceToHost, st));
-        CK(cudaMemcpyAsync(down + nj + 1, L.status, sizeof(uint32_t), cudaMemcpyDeviceToHost, st));
+        CK(cudaMemcpyAsync(down, L.counts, nj * sizeof(uint64_t), cudaMemcpyDeviceToHost, st));
+        CK(cudaMemcpyAsync(down + nj, L.status, sizeof(uint32_t), cudaMemcpyDeviceToHost, st));
         CK(cudaStreamSynchronize(st));
         if (g_timing) {
             g_stats.expand_ms += elapsed(g_ev.ev[0], g_ev.ev[1]);
             g_stats.compact_ms += elapsed(g_ev.ev[1], g_ev.ev[2]);
         }
-        uint32_t status = (uint32_t)(down[nj + 1] & 0xFFFFFFFFu);
-        if (status & kStatusTableFull) return SW_ENOMEM;
-        uint64_t total = down[nj];
-        std::vector<int64_t> rank(down, down + nj);
-        rank.push_back((int64_t)total);
-        // 3. new levels
+        if ((uint32_t)(down[nj] & 0xFFFFFFFFu) & kStatusTableFull) return SW_EINTERNAL;
+        // new levels; return the unused tail of each destination
         std::vector<int> advanced;
         for (int t = 0; t < nj; ++t) {
-            Inst &x = I[who[t]];
-            int d = dirs[t];
-            int64_t c = rank[t + 1] - rank[t];
-            int64_t nc = x.cnt[d].back() * x.k;
-            x.off[d].push_back(top + rank[t]);
-            x.cnt[d].push_back(c);
-            x.dupl[d] = 1.0 - (double)c / (double)nc;
-            x.stored += c;
-            if (c == 0) {
-                x.state = kFailed;
-                x.code = SW_ENOTSYNC;
-            } else {
-                advanced.push_back(who[t]);
-            }
+            Sel &s = sel[t];
+            Inst &x = I[s.id];
+            int64_t c = (int64_t)down[t];
+            set_pool.release(s.dest + c, s.nc - c);
+            x.lev[s.d].push_back({s.dest, c, c});
+            x.dupl[s.d] = 1.0 - (double)c / (double)s.nc;
+            x.stored[s.d] += c;
+            if (c == 0) finish(x, kFailed, SW_ENOTSYNC);
+            else advanced.push_back(s.id);
         }
-        top += (int64_t)total;
-        stored_total = top;
-        // 4. meet check on the advanced instances
+        // meet check on the advanced instances
         std::vector<int> met;
         std::vector<unsigned long long> best;
         if (!advanced.empty()) {
+            if (!stage_begin()) return SW_ECUDA;
             int nm = (int)advanced.size();
-            MeetJob *mj = (MeetJob *)g_up.get(nm * sizeof(MeetJob));
-            if (!mj) return SW_ECUDA;
+            MeetJob *d_mj;
+            MeetJob *mj = stg.take<MeetJob>(nm, &d_mj);
+            if (!stg.ok) return SW_EINTERNAL;
             const int64_t TF = mc.algo == 0 ? (int64_t)mc.tf_rows : (int64_t)mc.nt * mc.R;
             int64_t ntiles = 0;
             for (int t = 0; t < nm; ++t) {
                 Inst &x = I[advanced[t]];
                 MeetJob &M = mj[t];
-                M.f_off = x.off[0].back();
-                M.f_cnt = x.cnt[0].back();
-                M.b_off = x.off[1].back();
-                M.b_cnt = x.cnt[1].back();
+                M.f_off = x.lev[0].back().off;
+                M.f_cnt = x.lev[0].back().cnt;
+                M.b_off = x.lev[1].back().off;
+                M.b_cnt = x.lev[1].back().cnt;
                 M.tile_off = ntiles;
                 M.ntb = (M.b_cnt + mc.tb - 1) / mc.tb;
                 M.slot = t;
                 ntiles += ((M.f_cnt + TF - 1) / TF) * M.ntb;
             }
-            CK(cudaMemcpyAsync(L.mjobs, mj, nm * sizeof(MeetJob), cudaMemcpyHostToDevice, st));
+            rc = stage_flush();
+            if (rc) return rc;
             CK(cudaMemsetAsync(L.best, 0xFF, nm * sizeof(unsigned long long), st));
-            CK(cudaMemsetAsync(L.pairs, 0, 2 * sizeof(unsigned long long), st));
+            CK(cudaMemsetAsync(L.pairs, 0, 3 * sizeof(unsigned long long), st));
             if (g_timing) CK(cudaEventRecord(g_ev.ev[3], st));
-            CK(ops.meet(nm, ntiles, mc, L, st));
+            CK(ops.meet(d_mj, nm, ntiles, mc, L, st));
             if (g_timing) CK(cudaEventRecord(g_ev.ev[4], st));
             g_stats.meet_launches++;
-            unsigned long long *bd = (unsigned long long *)g_down.get((nm + 2) * sizeof(unsigned long long));
+            unsigned long long *bd = (unsigned long long *)g_down.get((nm + 3) * sizeof(unsigned long long));
             if (!bd) return SW_ECUDA;
             CK(cudaMemcpyAsync(bd, L.best, nm * sizeof(unsigned long long), cudaMemcpyDeviceToHost, st));
-            CK(cudaMemcpyAsync(bd + nm, L.pairs, 2 * sizeof(unsigned long long), cudaMemcpyDeviceToHost, st));
+            CK(cudaMemcpyAsync(bd + nm, L.pairs, 3 * sizeof(unsigned long long), cudaMemcpyDeviceToHost, st));
             CK(cudaStreamSynchronize(st));
             if (g_timing) g_stats.meet_ms += elapsed(g_ev.ev[3], g_ev.ev[4]);
             g_stats.pairs += (int64_t)bd[nm];
             g_stats.and_iters += (int64_t)bd[nm + 1];
+            g_stats.rows_transposed += (int64_t)bd[nm + 2];
             for (int t = 0; t < nm; ++t)
                 if (bd[t] != ~0ull) {
                     met.push_back(advanced[t]);
                     best.push_back(bd[t]);
                 }
         }
-        // 5. words of the instances that met
         if (!met.empty()) {
-            int rc = recover_words(met, best);
+            rc = recover_words(met, best);
             if (rc) return rc;
         }
-        // 6. drop finished instances from the active list
-        active.erase(std::remove_if(active.begin(), active.end(),
-                                    [&](int id) { return I[id].state != kActive; }),
+        active.erase(std::remove_if(active.begin(), active.end(), [&](int id) { return I[id].state != kActive; }),
                      active.end());
+        g_stats.arena_peak = std::max(g_stats.arena_peak, set_pool.used);
         return SW_OK;
     }
 
     int recover_words(const std::vector<int> &met, const std::vector<unsigned long long> &best) {
         size_t pos = 0;
         while (pos < met.size()) {
-            // a chunk of word jobs that fits the per-call areas
+            if (!stage_begin()) return SW_ECUDA;
             std::vector<WordJob> wj;
             std::vector<int64_t> blev;
             int64_t area = 0;
-            size_t first = pos;
             for (; pos < met.size(); ++pos) {
                 Inst &x = I[met[pos]];
-                int i = (int)x.cnt[0].size() - 1, j = (int)x.cnt[1].size() - 1;
+                int i = (int)x.lev[0].size() - 1, j = (int)x.lev[1].size() - 1;
                 int r = i + j;
                 x.r = r;
                 if (r > x.word_cap) {
-                    x.state = kFailed;
-                    x.code = SW_EWORDCAP;
+                    finish(x, kFailed, SW_EWORDCAP);
                     continue;
                 }
-                if (!device_words && area + r > L.word_area_cap && !wj.empty()) break;
-                if ((int64_t)(blev.size() / 2) + j > L.blevels_cap && !wj.empty()) break;
                 if (!device_words && r > L.word_area_cap) {
-                    x.state = kFailed;
-                    x.code = SW_ENOMEM;
+                    finish(x, kFailed, SW_ENOMEM);
                     continue;
                 }
+                size_t need = (wj.size() + 1) * sizeof(WordJob) + (blev.size() + 2 * j) * sizeof(int64_t) + 1024;
+                if (!wj.empty() && (!stg.fits(need) || (!device_words && area + r > L.word_area_cap))) break;
                 WordJob J;
-                J.f_arena = x.off[0].back() + (int64_t)(best[pos] >> 32);
+                J.f_arena = x.lev[0].back().off + (int64_t)(best[pos] >> 32);
                 J.blev = (int64_t)(blev.size() / 2);
                 J.word_off = device_words ? x.word_off : area;
                 J.delta_off = x.delta_off;
@@ -685,50 +906,53 @@ struct Search {
                 J.j = j;
                 J.n = x.n;
                 J.k = x.k;
-                J.slot = (int32_t)(pos - first);
+                J.slot = (int32_t)wj.size();
                 J.pad = met[pos];
                 for (int m = 0; m < j; ++m) {
-                    blev.push_back(x.off[1][m]);
-                    blev.push_back(x.cnt[1][m]);
+                    blev.push_back(x.lev[1][m].off);
+                    blev.push_back(x.lev[1][m].cnt);
                 }
                 if (!device_words) area += r;
                 wj.push_back(J);
             }
             if (wj.empty()) continue;
             int nw = (int)wj.size();
-            CK(cudaMemcpyAsync(L.wjobs, wj.data(), nw * sizeof(WordJob), cudaMemcpyHostToDevice, st));
-            if (!blev.empty())
-                CK(cudaMemcpyAsync(L.blevels, blev.data(), blev.size() * sizeof(int64_t), cudaMemcpyHostToDevice,
-                                   st));
+            WordJob *d_wj;
+            int64_t *d_bl;
+            WordJob *hw = stg.take<WordJob>(nw, &d_wj);
+            int64_t *hb = stg.take<int64_t>(std::max<size_t>(blev.size(), 2), &d_bl);
+            if (!stg.ok) return SW_EINTERNAL;
+            std::memcpy(hw, wj.data(), nw * sizeof(WordJob));
+            if (!blev.empty()) std::memcpy(hb, blev.data(), blev.size() * sizeof(int64_t));
+            int rc = stage_flush();
+            if (rc) return rc;
             uint8_t *base = device_words ? out_words : L.word_area;
-            CK(ops.words(nw, base, L, st));
+            CK(ops.words(d_wj, d_bl, nw, base, L, st));
             uint32_t *ws = (uint32_t *)g_down.get(nw * sizeof(uint32_t));
             if (!ws) return SW_ECUDA;
             CK(cudaMemcpyAsync(ws, L.word_status, nw * sizeof(uint32_t), cudaMemcpyDeviceToHost, st));
-            uint8_t *hw = nullptr;
+            uint8_t *hwd = nullptr;
             if (!device_words && area > 0) {
-                hw = (uint8_t *)g_words.get((size_t)area);
-                if (!hw) return SW_ECUDA;
-                CK(cudaMemcpyAsync(hw, L.word_area, (size_t)area, cudaMemcpyDeviceToHost, st));
+                hwd = (uint8_t *)g_words.get((size_t)area);
+                if (!hwd) return SW_ECUDA;
+                CK(cudaMemcpyAsync(hwd, L.word_area, (size_t)area, cudaMemcpyDeviceToHost, st));
             }
             CK(cudaStreamSynchronize(st));
             for (int t = 0; t < nw; ++t) {
                 Inst &x = I[wj[t].pad];
                 if (ws[t] != 0) {
-                    x.state = kFailed;
-                    x.code = SW_EINTERNAL;
+                    finish(x, kFailed, SW_EINTERNAL);
                     continue;
                 }
                 if (!device_words && out_words)
-                    std::memcpy(out_words + x.word_off, hw + wj[t].word_off, (size_t)x.r);
-                x.state = kDone;
-                x.code = SW_OK;
+                    std::memcpy(out_words + x.word_off, hwd + wj[t].word_off, (size_t)x.r);
+                finish(x, kDone, SW_OK);
             }
         }
         return SW_OK;
     }
 
-    // Runs every instance (state kWaiting) to completion, in waves.
+    // Runs every waiting instance to completion.
     int run() {
         std::vector<int> queue;
         for (size_t t = 0; t < I.size(); ++t) {
@@ -736,64 +960,37 @@ struct Search {
             if (x.state != kWaiting) continue;
             if (x.n == 1) {  // Q is already a singleton: r = 0
                 x.r = 0;
+                x.sizes[0] = {1};
+                x.sizes[1] = {1};
                 x.state = kDone;
                 x.code = SW_OK;
-                x.off[0] = {0};
-                x.cnt[0] = {1};
-                x.off[1] = {0};
-                x.cnt[1] = {1};
                 continue;
             }
             queue.push_back((int)t);
         }
-        size_t limit = queue.size();
         while (!queue.empty()) {
-            // admit as many as the roots allow (and fewer after evictions)
-            std::vector<int> wave;
-            int64_t need = 0;
-            std::vector<int> rest;
-            for (int id : queue) {
-                int64_t s = I[id].n + 1;
-                if (wave.size() < limit && need + s <= L.cap_sets && 2 * (need + s) <= (int64_t)L.cap_table) {
-                    wave.push_back(id);
-                    need += s;
-                } else {
-                    rest.push_back(id);
-                }
-            }
-            if (wave.empty()) {
-                for (int id : queue) {
-                    I[id].state = kFailed;
-                    I[id].code = SW_ENOMEM;
-                }
-                break;
-            }
-            int rc = start_wave(wave);
-            if (rc) return rc;
-            std::vector<int> active = wave, evicted;
-            while (!active.empty()) {
-                rc = iterate(active, evicted);
-                if (rc == SW_ENOMEM) {  // table overflow: retry the unfinished ones later
-                    for (int id : active) {
-                        I[id].state = kWaiting;
-                        I[id].evictions++;
-                        g_stats.evictions++;
-                        evicted.push_back(id);
+            g_stats.waves++;
+            size_t first = 0;
+            while (first < queue.size() || !active.empty()) {
+                if (first < queue.size()) {
+                    size_t taken = 0;
+                    int rc = admit(queue, first, &taken);
+                    if (rc) return rc;
+                    first += taken;
+                    if (active.empty() && taken == 0) {  // a single instance's roots do not fit
+                        Inst &x = I[queue[first]];
+                        x.state = kFailed;
+                        x.code = SW_ENOMEM;
+                        ++first;
+                        continue;
                     }
-                    active.clear();
-                    break;
                 }
+                if (active.empty()) continue;
+                int rc = iterate();
                 if (rc) return rc;
             }
-            g_stats.arena_peak = std::max(g_stats.arena_peak, top_peak());
-            if (wave.size() == 1 && !evicted.empty()) {  // it had the whole workspace
-                I[evicted[0]].state = kFailed;
-                I[evicted[0]].code = SW_ENOMEM;
-                evicted.clear();
-            }
-            if (!evicted.empty()) limit = std::max<size_t>(1, std::min(limit, wave.size()) / 2);
-            queue = evicted;
-            queue.insert(queue.end(), rest.begin(), rest.end());
+            queue.swap(deferred);
+            deferred.clear();
         }
         return SW_OK;
     }
@@ -806,12 +1003,161 @@ int32_t common_w(const std::vector<Inst> &I) {
 }
 
 void store_sizes(sw_automaton *h, const Inst &x) {
-    h->fwd_sizes = x.cnt[0];
-    h->bwd_sizes = x.cnt[1];
+    h->fwd_sizes = x.sizes[0];
+    h->bwd_sizes = x.sizes[1];
     h->searched = true;
 }
 
 }  // namespace
+
+// ---------------------------------------------------------------- serving
+
+// Continuous batching: a worker thread owns the stream and one engine.  It
+// moves submitted requests into the engine's queue, admits them while the
+// set and table pools are below the admission budget, advances every
+// admitted request by one level per iteration (all in the same launches),
+// and posts finished requests to the completion queue.
+struct sw_server {
+    int W = 1, n_max = 1, k_max = 1, cap = 0, word_cap = 0;
+    double admit_frac = 0.5;
+    cudaStream_t st = nullptr;
+    Layout L;
+    sw_options opt;
+    std::vector<Inst> slots;
+    std::vector<int> free_slots;
+    std::vector<uint64_t> req_of;
+    std::vector<uint8_t> words;  // word_cap bytes per slot
+    Pool delta_pool;
+    std::unique_ptr<Engine> eng;
+    // submitted, not yet taken by the worker
+    struct Sub {
+        uint64_t req;
+        int32_t n, k;
+        std::vector<uint16_t> delta;
+    };
+    std::deque<Sub> incoming;
+    std::deque<int> queue;  // slots waiting for admission
+    struct Done {
+        uint64_t req;
+        int32_t r, code;
+        std::vector<uint8_t> word;
+    };
+    std::deque<Done> done;
+    std::mutex mu;
+    std::condition_variable cv;
+    std::atomic<bool> stop{false};
+    std::atomic<int32_t> fatal{SW_OK};
+    std::atomic<int32_t> n_active{0}, n_queued{0};
+    std::thread worker;
+
+    void loop();
+    int admit_some();
+    void collect();
+};
+
+int sw_server::admit_some() {
+    // take submissions into free slots (their delta tables go to the device)
+    {
+        std::lock_guard<std::mutex> lk(mu);
+        while (!incoming.empty() && !free_slots.empty()) {
+            Sub &sb = incoming.front();
+            int64_t doff = delta_pool.alloc((int64_t)sb.n * sb.k);
+            if (doff < 0) break;
+            int id = free_slots.back();
+            free_slots.pop_back();
+            Inst x;
+            x.n = sb.n;
+            x.k = sb.k;
+            x.orig = id;
+            x.delta_off = doff;
+            x.word_off = (int64_t)id * word_cap;
+            x.word_cap = word_cap;
+            slots[id] = x;
+            req_of[id] = sb.req;
+            if (cudaMemcpyAsync(L.delta16 + doff, sb.delta.data(), sb.delta.size() * sizeof(uint16_t),
+                                cudaMemcpyHostToDevice, st) != cudaSuccess ||
+                cudaStreamSynchronize(st) != cudaSuccess)
+                return SW_ECUDA;
+            queue.push_back(id);
+            incoming.pop_front();
+        }
+    }
+    // n = 1 needs no search
+    for (auto it = queue.begin(); it != queue.end();) {
+        Inst &x = slots[*it];
+        if (x.n == 1) {
+            x.r = 0;
+            x.state = kDone;
+            x.code = SW_OK;
+            it = queue.erase(it);
+        } else {
+            ++it;
+        }
+    }
+    // admission by memory budget
+    std::vector<int> ids;
+    while (!queue.empty()) {
+        if ((double)eng->set_pool.used > admit_frac * (double)eng->set_pool.cap ||
+            (double)eng->tab_pool.used > admit_frac * (double)eng->tab_pool.cap)
+            break;
+        ids.assign(1, queue.front());
+        size_t taken = 0;
+        int rc = eng->admit(ids, 0, &taken);
+        if (rc) return rc;
+        if (!taken) break;
+        queue.pop_front();
+    }
+    n_queued = (int32_t)queue.size();
+    return SW_OK;
+}
+
+void sw_server::collect() {
+    std::lock_guard<std::mutex> lk(mu);
+    for (size_t id = 0; id < slots.size(); ++id) {
+        Inst &x = slots[id];
+        if (x.state != kDone && x.state != kFailed) continue;
+        Done d;
+        d.req = req_of[id];
+        d.code = x.code;
+        d.r = (x.state == kDone || x.code == SW_EWORDCAP) ? x.r : -1;
+        if (x.state == kDone) d.word.assign(words.begin() + x.word_off, words.begin() + x.word_off + x.r);
+        done.push_back(std::move(d));
+        delta_pool.release(x.delta_off, (int64_t)x.n * x.k);
+        x = Inst{};
+        x.state = -1;  // free
+        free_slots.push_back((int)id);
+    }
+}
+
+void sw_server::loop() {
+    g_opt = opt;
+    for (;;) {
+        if (stop) break;
+        int rc = admit_some();
+        if (rc) {
+            fatal = rc;
+            break;
+        }
+        // requests set back by an eviction go to the front of the queue
+        for (int id : eng->deferred) queue.push_front(id);
+        eng->deferred.clear();
+        collect();
+        cv.notify_all();
+        n_active = (int32_t)eng->active.size();
+        if (eng->active.empty()) {
+            std::unique_lock<std::mutex> lk(mu);
+            cv.wait_for(lk, std::chrono::milliseconds(2), [&] { return stop || !incoming.empty(); });
+            continue;
+        }
+        rc = eng->iterate();
+        if (rc) {
+            fatal = rc;
+            break;
+        }
+        collect();
+        cv.notify_all();
+    }
+}
 
 // ==================================================================== C-ABI
 
@@ -868,8 +1214,8 @@ size_t sw_workspace_min_bytes(int32_t n_max, int32_t k_max, int32_t count) {
     if (n_max < 1 || k_max < 1 || count < 1) return 0;
     int W = words_for(n_max);
     int64_t delta = (int64_t)n_max * k_max * count;
-    double per_set = (8.0 * W + 12) + 1.0 * (8.0 * W + 17) + 32.0;
-    return small_area_bytes(count, delta) + (size_t)(per_set * ((double)count * (n_max + 1) * 4 + 4096)) + (1 << 20);
+    double per_set = (8.0 * W + 8) / 0.55;
+    return small_area_bytes(count, delta) + (size_t)(per_set * ((double)count * (n_max + 1) * 8 + 8192)) + (1 << 20);
 }
 
 static int32_t run_instances(std::vector<Inst> &I, const std::vector<uint16_t> *host_delta,
@@ -878,15 +1224,11 @@ static int32_t run_instances(std::vector<Inst> &I, const std::vector<uint16_t> *
     g_stats = Stats{};
     if (g_timing) g_ev.ensure();
     int W = common_w(I);
-    int kmax = 1;
     int64_t delta_elems = 0;
-    for (auto &x : I) {
-        kmax = std::max(kmax, x.k);
-        delta_elems = std::max(delta_elems, x.delta_off + (int64_t)x.n * x.k);
-    }
+    for (auto &x : I) delta_elems = std::max(delta_elems, x.delta_off + (int64_t)x.n * x.k);
     Layout L;
     if (((uintptr_t)ws & 255) != 0) return SW_EINVAL;
-    if (!carve(ws, ws_bytes, W, (int32_t)I.size(), delta_elems, kmax, L)) return SW_ENOMEM;
+    if (!carve(ws, ws_bytes, W, (int32_t)I.size(), delta_elems, L)) return SW_ENOMEM;
     if (host_delta) {
         void *up = g_up.get(host_delta->size() * sizeof(uint16_t));
         if (!up) return SW_ECUDA;
@@ -897,8 +1239,10 @@ static int32_t run_instances(std::vector<Inst> &I, const std::vector<uint16_t> *
             return SW_ECUDA;
     } else {
         // device int32 tables -> uint16, one launch for all instances
-        // (grid.y <= 65535 instances per launch)
+        // (grid.y <= 65535 instances per launch); the job rows are staged in
+        // the mirror area
         size_t nI = I.size();
+        if (nI * sizeof(ConvJob) + 256 > L.mirror_bytes) return SW_EINTERNAL;
         ConvJob *cj = (ConvJob *)g_up.get(nI * sizeof(ConvJob) + 64);
         if (!cj) return SW_ECUDA;
         int64_t maxcnt = 1;
@@ -906,10 +1250,7 @@ static int32_t run_instances(std::vector<Inst> &I, const std::vector<uint16_t> *
             cj[t] = ConvJob{(*src_off)[t], I[t].delta_off, (int64_t)I[t].n * I[t].k, I[t].n, 0};
             maxcnt = std::max(maxcnt, cj[t].count);
         }
-        // ConvJob rows go where the expansion jobs will later be staged
-        ConvJob *d_cj = (ConvJob *)L.jobs;
-        if (nI * sizeof(ConvJob) > (size_t)std::max<int32_t>((int32_t)I.size(), 1) * sizeof(ExpandJob))
-            return SW_EINTERNAL;
+        ConvJob *d_cj = (ConvJob *)L.mirror;
         if (cudaMemsetAsync(L.status, 0, sizeof(uint32_t), st) != cudaSuccess ||
             cudaMemcpyAsync(d_cj, cj, nI * sizeof(ConvJob), cudaMemcpyHostToDevice, st) != cudaSuccess)
             return SW_ECUDA;
@@ -927,11 +1268,11 @@ static int32_t run_instances(std::vector<Inst> &I, const std::vector<uint16_t> *
             return SW_ECUDA;
         if (*bad) return SW_EINVAL;
     }
-    Search S(W, st, I);
-    S.L = L;
-    S.device_words = device_words;
-    S.out_words = out_words;
-    int rc = S.run();
+    if (cudaMemsetAsync(L.status, 0, sizeof(uint32_t), st) != cudaSuccess) return SW_ECUDA;
+    Engine E(W, st, I, L);
+    E.device_words = device_words;
+    E.out_words = out_words;
+    int rc = E.run();
     if (rc == SW_OK && cudaStreamSynchronize(st) != cudaSuccess) rc = SW_ECUDA;
     return rc;
 }
@@ -1059,7 +1400,8 @@ int32_t sw_batch_device(int32_t count, const int32_t *n, const int32_t *k, const
 
 int32_t sw_last_stats(int64_t *pairs, int64_t *candidates, int32_t *iterations, double *meet_ms,
                       double *expand_ms, double *compact_ms, int32_t *meet_launches, int64_t *launches,
-                      int32_t *waves, int32_t *evictions, int64_t *arena_peak, int64_t *and_iters) {
+                      int32_t *waves, int32_t *evictions, int64_t *arena_peak, int64_t *and_iters,
+                      int64_t *rows_transposed) {
     if (pairs) *pairs = g_stats.pairs;
     if (candidates) *candidates = g_stats.candidates;
     if (iterations) *iterations = g_stats.iterations;
@@ -1072,6 +1414,7 @@ int32_t sw_last_stats(int64_t *pairs, int64_t *candidates, int32_t *iterations, 
     if (evictions) *evictions = g_stats.evictions;
     if (arena_peak) *arena_peak = g_stats.arena_peak;
     if (and_iters) *and_iters = g_stats.and_iters;
+    if (rows_transposed) *rows_transposed = g_stats.rows_transposed;
     return SW_OK;
 }
 
@@ -1085,10 +1428,98 @@ void sw_set_options(const sw_options *opt) {
     if (!opt) return;
     g_opt = *opt;
     if (!(g_opt.dir_theta > 0) || !std::isfinite(g_opt.dir_theta)) g_opt.dir_theta = 1.0;
-    if (!(g_opt.set_cost >= 0) || !std::isfinite(g_opt.set_cost)) g_opt.set_cost = 16384.0;
+    if (!(g_opt.set_cost >= 0) || !std::isfinite(g_opt.set_cost)) g_opt.set_cost = 8192.0;
     if (g_opt.meet_b_tile < 0) g_opt.meet_b_tile = 0;
     if (g_opt.meet_algo != 1) g_opt.meet_algo = 0;
     if (g_opt.meet_f_rows < 0) g_opt.meet_f_rows = 0;
+}
+
+int32_t sw_server_create(void *workspace, size_t ws_bytes, int32_t n_max, int32_t k_max, int32_t max_requests,
+                         int32_t word_cap, void *stream, sw_server **out) {
+    if (!out || !workspace || n_max < 1 || n_max > SW_MAX_STATES || k_max < 1 || k_max > SW_MAX_LETTERS ||
+        max_requests < 1 || word_cap < 1)
+        return fail(SW_EINVAL);
+    if (((uintptr_t)workspace & 255) != 0) return fail(SW_EINVAL);
+    std::unique_ptr<sw_server> s(new (std::nothrow) sw_server);
+    if (!s) return fail(SW_ENOMEM);
+    s->W = words_for(n_max);
+    s->n_max = n_max;
+    s->k_max = k_max;
+    s->cap = max_requests;
+    s->word_cap = word_cap;
+    s->st = (cudaStream_t)stream;
+    s->opt = g_opt;
+    if (!carve(workspace, ws_bytes, s->W, max_requests, (int64_t)max_requests * n_max * k_max, s->L))
+        return fail(SW_ENOMEM);
+    if (cudaMemsetAsync(s->L.status, 0, sizeof(uint32_t), s->st) != cudaSuccess ||
+        cudaStreamSynchronize(s->st) != cudaSuccess)
+        return fail(SW_ECUDA);
+    s->slots.assign((size_t)max_requests, Inst{});
+    for (auto &x : s->slots) x.state = -1;
+    s->req_of.assign((size_t)max_requests, 0);
+    s->words.assign((size_t)max_requests * word_cap, 0);
+    for (int i = max_requests - 1; i >= 0; --i) s->free_slots.push_back(i);
+    s->delta_pool.init(s->L.delta_cap);
+    s->eng.reset(new Engine(s->W, s->st, s->slots, s->L));
+    s->eng->device_words = false;
+    s->eng->out_words = s->words.data();
+    sw_server *raw = s.get();
+    raw->worker = std::thread([raw] { raw->loop(); });
+    *out = s.release();
+    g_last_error = SW_OK;
+    return SW_OK;
+}
+
+int32_t sw_server_submit(sw_server *s, sw_handle h, uint64_t req_id) {
+    if (!s || !h) return fail(SW_EINVAL);
+    if (h->n > s->n_max || h->k > s->k_max) return fail(SW_EINVAL);
+    if (s->fatal != SW_OK) return fail(s->fatal);
+    {
+        std::lock_guard<std::mutex> lk(s->mu);
+        if ((int32_t)s->incoming.size() >= s->cap) return fail(SW_EBUSY);
+        s->incoming.push_back(sw_server::Sub{req_id, h->n, h->k, h->delta16});
+    }
+    s->cv.notify_all();
+    g_last_error = SW_OK;
+    return SW_OK;
+}
+
+int32_t sw_server_poll(sw_server *s, uint64_t *req_id, int32_t *r, uint8_t *word, int32_t word_cap,
+                       int32_t *code) {
+    if (!s || !req_id || !r) return fail(SW_EINVAL);
+    std::lock_guard<std::mutex> lk(s->mu);
+    if (s->done.empty()) {
+        if (s->fatal != SW_OK) return fail(s->fatal);
+        return SW_EAGAIN;
+    }
+    sw_server::Done d = std::move(s->done.front());
+    s->done.pop_front();
+    *req_id = d.req;
+    *r = d.r;
+    if (code) *code = d.code;
+    if (word && d.code == SW_OK) {
+        if ((int32_t)d.word.size() > word_cap) return fail(SW_EWORDCAP);
+        std::memcpy(word, d.word.data(), d.word.size());
+    }
+    return SW_OK;
+}
+
+int32_t sw_server_pending(sw_server *s, int32_t *queued, int32_t *active, int32_t *finished) {
+    if (!s) return fail(SW_EINVAL);
+    std::lock_guard<std::mutex> lk(s->mu);
+    if (queued) *queued = (int32_t)s->incoming.size() + s->n_queued;
+    if (active) *active = s->n_active;
+    if (finished) *finished = (int32_t)s->done.size();
+    return s->fatal;
+}
+
+void sw_server_destroy(sw_server *s) {
+    if (!s) return;
+    s->stop = true;
+    s->cv.notify_all();
+    if (s->worker.joinable()) s->worker.join();
+    cudaStreamSynchronize(s->st);
+    delete s;
 }
 
 }  // extern "C"

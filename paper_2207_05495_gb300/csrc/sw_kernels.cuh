@@ -2,11 +2,12 @@
 //
 // A subset of Q is stored as W 64-bit words (state q at bit q%64 of word
 // q/64; bits >= n are zero).  All levels of all instances and both
-// directions live in one arena of sets; each stored set has a parent link
-// ((parent arena index) << 8 | letter) and an owner tag (instance << 1 |
-// direction).  One open-addressing hash table over the arena holds, per
-// (instance, direction), every set seen so far: it removes duplicates
-// within a level and sets of earlier levels (the equality history).
+// directions live in one arena of sets (each level contiguous, placed by the
+// host's pool allocator); a forward set also has a parent link ((parent
+// arena index) << 8 | letter).  Every (instance, direction) owns an
+// open-addressing hash table in a table pool holding the arena indices of
+// every set it has seen: it removes duplicates within a level and sets of
+// earlier levels (the equality history).
 #pragma once
 
 #include <cstdint>
@@ -16,19 +17,21 @@ namespace sw {
 
 constexpr uint64_t kEmpty = ~0ull;
 constexpr uint64_t kCand = 1ull << 62;  // slot value kCand + c: candidate c (this expansion)
-constexpr int kScanBlock = 1024;        // candidates per block in flag/compact
+constexpr int kScanBlock = 512;         // candidates per block in flag/compact
 constexpr int kScanThreads = 256;
 constexpr int kMaxProbe = 1 << 14;
 
 enum : uint32_t { kStatusTableFull = 1u, kStatusWordFail = 2u, kStatusVerifyFail = 4u };
 
 struct ExpandJob {
-    int64_t cand_off;    // first candidate id
+    int64_t cand_off;    // first candidate id (a multiple of kScanBlock)
     int64_t parent_off;  // arena index of the parent level's first set
     int64_t parent_cnt;
     int64_t delta_off;   // instance's uint16 [k][n] table in delta16
-    int32_t owner;       // instance << 1 | direction (0 forward, 1 backward)
-    int32_t n, k, pad;
+    int64_t dest_off;    // arena index where the new level starts
+    int64_t tab_off;     // the (instance, direction) hash table
+    int64_t tab_cap;
+    int32_t dir, n, k, pad;  // dir 0 forward (images), 1 backward (preimages)
 };
 
 struct MeetJob {
@@ -39,8 +42,20 @@ struct MeetJob {
 };
 
 struct RootJob {
-    int64_t arena_off;   // F_0 = {Q} here, then the n singletons
-    int32_t inst, n;
+    int64_t f_off, b_off;         // F_0 = {Q} at f_off; B_0 = the n singletons at b_off
+    int64_t tab_off[2], tab_cap[2];
+    int32_t n, pad;
+};
+
+struct FillJob {
+    int64_t off, len;             // table slots to set to kEmpty
+};
+
+struct RehashSeg {
+    int64_t flat_off;             // first flat index of this segment
+    int64_t set_off, cnt;         // stored sets to re-enter
+    int64_t tab_off, tab_cap;     // into this table
+    int32_t dir, pad;
 };
 
 struct WordJob {
@@ -160,44 +175,83 @@ __device__ __forceinline__ int find_job_expand(const ExpandJob *__restrict__ job
     return lo;
 }
 
-// ------------------------------------------------------------ roots
+// Linear probing inside one table [tab_off, tab_off + tab_cap): the next slot.
+__device__ __forceinline__ uint64_t next_slot(uint64_t pos, int64_t tab_off, int64_t tab_cap) {
+    return (pos + 1 == (uint64_t)(tab_off + tab_cap)) ? (uint64_t)tab_off : pos + 1;
+}
+
+// Enters the stored set g (no equal set is present) into a table.
+template <int W>
+__device__ __forceinline__ void insert_stored(uint64_t *table, int64_t tab_off, int64_t tab_cap, uint32_t dir,
+                                              const uint64_t (&s)[W], int64_t g, uint32_t *status) {
+    uint64_t pos = (uint64_t)tab_off + __umul64hi(hash_set<W>(dir, s), (uint64_t)tab_cap);
+    for (int probe = 0; probe < kMaxProbe; ++probe) {
+        unsigned long long old = atomicCAS((unsigned long long *)(table + pos), kEmpty, (unsigned long long)g);
+        if (old == kEmpty) return;
+        pos = next_slot(pos, tab_off, tab_cap);
+    }
+    atomicOr(status, kStatusTableFull);
+}
+
+// ------------------------------------------------------------ roots, fill, rehash
 
 // F_0 = {Q} and B_0 = the n singletons of each new instance (Alg. 1,
-// initialisation), stored and entered into the table.  One thread per set.
+// initialisation), stored and entered into their tables.  One thread per
+// set; blockIdx.y = instance.
 template <int W>
-__global__ void k_roots(const RootJob *__restrict__ jobs, int njobs, uint64_t *__restrict__ sets,
-                        uint64_t *__restrict__ link, uint32_t *__restrict__ owner,
-                        uint64_t *__restrict__ table, uint64_t cap_table, uint32_t *status) {
+__global__ void k_roots(const RootJob *__restrict__ jobs, uint64_t *__restrict__ sets,
+                        uint64_t *__restrict__ link, uint64_t *table, uint32_t *status) {
     const RootJob J = jobs[blockIdx.y];
     for (int t = blockIdx.x * blockDim.x + threadIdx.x; t <= J.n; t += gridDim.x * blockDim.x) {
         uint64_t s[W];
-        uint32_t own;
+        int64_t g;
+        uint32_t dir;
         if (t == 0) {  // Q: the first n bits
 #pragma unroll
             for (int w = 0; w < W; ++w) {
                 int lo = w * 64;
                 s[w] = (J.n >= lo + 64) ? ~0ull : (J.n > lo ? ((1ull << (J.n - lo)) - 1) : 0ull);
             }
-            own = (uint32_t)J.inst << 1;
+            g = J.f_off;
+            dir = 0;
+            link[g] = ~0ull;
         } else {
             int q = t - 1;
 #pragma unroll
             for (int w = 0; w < W; ++w) s[w] = ((q >> 6) == w) ? (1ull << (q & 63)) : 0ull;
-            own = ((uint32_t)J.inst << 1) | 1u;
+            g = J.b_off + q;
+            dir = 1;
         }
-        int64_t g = J.arena_off + t;
 #pragma unroll
         for (int w = 0; w < W; ++w) sets[g * W + w] = s[w];
-        link[g] = ~0ull;
-        owner[g] = own;
-        uint64_t pos = __umul64hi(hash_set<W>(own, s), cap_table);
-        int probe = 0;
-        for (; probe < kMaxProbe; ++probe) {
-            unsigned long long old = atomicCAS((unsigned long long *)(table + pos), kEmpty, (unsigned long long)g);
-            if (old == kEmpty) break;
-            pos = (pos + 1 == cap_table) ? 0 : pos + 1;
+        insert_stored<W>(table, J.tab_off[dir], J.tab_cap[dir], dir, s, g, status);
+    }
+}
+
+// Sets table slots to kEmpty; blockIdx.y = job.
+__global__ void k_fill(const FillJob *__restrict__ jobs, uint64_t *__restrict__ table) {
+    const FillJob J = jobs[blockIdx.y];
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < J.len; i += (int64_t)gridDim.x * blockDim.x)
+        table[J.off + i] = kEmpty;
+}
+
+// Re-enters every stored set of a growing (instance, direction) into its
+// new, larger table.  Flat over all segments.
+template <int W>
+__global__ void k_rehash(const RehashSeg *__restrict__ segs, int nseg, int64_t total,
+                         const uint64_t *__restrict__ sets, uint64_t *table, uint32_t *status) {
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total;
+         t += (int64_t)gridDim.x * blockDim.x) {
+        int lo = 0, hi = nseg - 1;
+        while (lo < hi) {
+            int mid = (lo + hi + 1) >> 1;
+            if (segs[mid].flat_off <= t) lo = mid; else hi = mid - 1;
         }
-        if (probe == kMaxProbe) atomicOr(status, kStatusTableFull);
+        const RehashSeg &S = segs[lo];
+        int64_t g = S.set_off + (t - S.flat_off);
+        uint64_t s[W];
+        load_set<W>(sets + g * W, s);
+        insert_stored<W>(table, S.tab_off, S.tab_cap, (uint32_t)S.dir, s, g, status);
     }
 }
 
@@ -206,28 +260,31 @@ __global__ void k_roots(const RootJob *__restrict__ jobs, int njobs, uint64_t *_
 // CalculateImages / CalculatePreimages (Alg. 1) fused with duplicate
 // removal and the equality history: candidate c = p*k + a of a job is the
 // image (forward) or preimage (backward) of parent p under letter a.  It is
-// written to cand_sets and entered into the table; among equal sets of one
-// (instance, direction) the smallest candidate id keeps the slot
-// (atomicMin), and a set already stored (an earlier level) is dropped.
-// cand_slot[c] = its slot, or -1 when dropped (duplicate of history, empty
-// preimage, or table overflow, which also raises kStatusTableFull).
+// written to cand_sets and entered into its (instance, direction) table;
+// among equal sets the smallest candidate id keeps the slot (atomicMin), and
+// a set already stored (an earlier level) is dropped.  cand_slot[c] = its
+// slot, or -1 when dropped (duplicate of history, empty preimage, padding
+// between jobs, or table overflow, which also raises kStatusTableFull).
 template <int W>
 __global__ void __launch_bounds__(256) k_expand(
     const ExpandJob *__restrict__ jobs, int njobs, int64_t ncand, const uint16_t *__restrict__ delta16,
-    const uint64_t *__restrict__ sets, const uint32_t *__restrict__ owner, uint64_t *table,
-    uint64_t cap_table, uint64_t *cand_sets, uint32_t *cand_owner, int64_t *__restrict__ cand_slot,
+    const uint64_t *__restrict__ sets, uint64_t *table, uint64_t *cand_sets, int64_t *__restrict__ cand_slot,
     uint32_t *status) {
     for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < ncand;
          c += (int64_t)gridDim.x * blockDim.x) {
         const ExpandJob &J = jobs[find_job_expand(jobs, njobs, c)];
         int64_t local = c - J.cand_off;
         int64_t p = local / J.k;
+        if (p >= J.parent_cnt) {  // padding up to the next job's block
+            cand_slot[c] = -1;
+            continue;
+        }
         int a = (int)(local - p * J.k);
         uint64_t S[W], T[W];
         load_set<W>(sets + (J.parent_off + p) * W, S);
         const uint16_t *da = delta16 + J.delta_off + (int64_t)a * J.n;
-        const uint32_t own = (uint32_t)J.owner;
-        if ((own & 1u) == 0) image<W>(S, da, T);
+        const uint32_t dir = (uint32_t)J.dir;
+        if (dir == 0) image<W>(S, da, T);
         else preimage<W>(S, da, J.n, T);
         bool empty = true;
 #pragma unroll
@@ -238,10 +295,9 @@ __global__ void __launch_bounds__(256) k_expand(
         }
 #pragma unroll
         for (int w = 0; w < W; ++w) cand_sets[c * W + w] = T[w];
-        cand_owner[c] = own;
         __threadfence();  // publish the set before its id can be seen in the table
         const uint64_t me = kCand + (uint64_t)c;
-        uint64_t pos = __umul64hi(hash_set<W>(own, T), cap_table);
+        uint64_t pos = (uint64_t)J.tab_off + __umul64hi(hash_set<W>(dir, T), (uint64_t)J.tab_cap);
         int64_t result = -1;
         int probe = 0;
         for (; probe < kMaxProbe; ++probe) {
@@ -253,17 +309,17 @@ __global__ void __launch_bounds__(256) k_expand(
                 v = old;
             }
             __threadfence();  // order the reads of v's set after observing v
-            if (v < kCand) {  // a stored set (earlier level or earlier kernel)
-                if (owner[v] == own && set_equal<W>(T, sets + v * W)) break;  // seen before: drop
+            if (v < kCand) {  // a stored set (earlier level)
+                if (set_equal<W>(T, sets + v * W)) break;  // seen before: drop
             } else {
                 uint64_t c2 = v - kCand;
-                if (ld_relaxed32(cand_owner + c2) == own && set_equal_cg<W>(T, cand_sets + c2 * W)) {
+                if (set_equal_cg<W>(T, cand_sets + c2 * W)) {
                     atomicMin((unsigned long long *)slot, (unsigned long long)me);
                     result = (int64_t)pos;
                     break;
                 }
             }
-            pos = (pos + 1 == cap_table) ? 0 : pos + 1;
+            pos = next_slot(pos, J.tab_off, J.tab_cap);
         }
         if (probe == kMaxProbe) atomicOr(status, kStatusTableFull);
         cand_slot[c] = result;
@@ -340,16 +396,16 @@ __global__ void __launch_bounds__(1024) k_scan_blocks(int64_t nblocks, const uin
 }
 
 // Survivors, in candidate order (= the canonical (parent, letter) order),
-// are appended to the arena at arena_top + their rank; their parent link and
-// owner are stored and their table slot is switched from the candidate id to
-// the arena index.  job_rank[J] = rank of job J's first candidate.
+// are written to their job's new level at dest_off + (rank within the job);
+// a job's candidates start on a block boundary, so its first rank is
+// block_off of that block.  Forward survivors get their parent link; every
+// survivor's table slot is switched from the candidate id to its arena index.
 template <int W>
 __global__ void __launch_bounds__(kScanThreads) k_compact(
     const ExpandJob *__restrict__ jobs, int njobs, int64_t ncand, const uint8_t *__restrict__ flag,
     const uint64_t *__restrict__ block_off, const uint64_t *__restrict__ cand_sets,
-    const uint32_t *__restrict__ cand_owner, const int64_t *__restrict__ cand_slot, uint64_t *__restrict__ table,
-    int64_t arena_top, uint64_t *__restrict__ sets, uint64_t *__restrict__ link, uint32_t *__restrict__ owner,
-    uint64_t *__restrict__ job_rank) {
+    const int64_t *__restrict__ cand_slot, uint64_t *__restrict__ table, uint64_t *__restrict__ sets,
+    uint64_t *__restrict__ link) {
     constexpr int IPT = kScanBlock / kScanThreads;
     int64_t base = (int64_t)blockIdx.x * kScanBlock + threadIdx.x * IPT;
     uint8_t f[IPT];
@@ -359,8 +415,7 @@ __global__ void __launch_bounds__(kScanThreads) k_compact(
         f[i] = (base + i < ncand) ? flag[base + i] : 0;
         cnt += f[i];
     }
-    // exclusive block scan of cnt
-    uint32_t x = cnt;
+    uint32_t x = cnt;  // inclusive warp scan, then across warps
     for (int o = 1; o < 32; o <<= 1) {
         uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
         if ((threadIdx.x & 31) >= o) x += y;
@@ -368,29 +423,37 @@ __global__ void __launch_bounds__(kScanThreads) k_compact(
     __shared__ uint32_t ws[kScanThreads / 32];
     if ((threadIdx.x & 31) == 31) ws[threadIdx.x >> 5] = x;
     __syncthreads();
+    if (cnt == 0) return;
     uint32_t wbefore = 0;
     for (int i = 0; i < (int)(threadIdx.x >> 5); ++i) wbefore += ws[i];
     uint64_t rank = block_off[blockIdx.x] + wbefore + x - cnt;
+    const ExpandJob &J = jobs[find_job_expand(jobs, njobs, base)];
+    const uint64_t first = block_off[J.cand_off / kScanBlock];
 #pragma unroll
     for (int i = 0; i < IPT; ++i) {
+        if (!f[i]) continue;
         int64_t c = base + i;
-        if (c >= ncand) break;
-        int ji = find_job_expand(jobs, njobs, c);
-        const ExpandJob &J = jobs[ji];
-        if (c == J.cand_off) job_rank[ji] = rank;
-        if (f[i]) {
-            int64_t g = arena_top + (int64_t)rank;
+        int64_t g = J.dest_off + (int64_t)(rank - first);
+#pragma unroll
+        for (int w = 0; w < W; ++w) sets[g * W + w] = cand_sets[c * W + w];
+        if (J.dir == 0) {
             int64_t local = c - J.cand_off;
             int64_t p = local / J.k;
-            int64_t a = local - p * J.k;
-#pragma unroll
-            for (int w = 0; w < W; ++w) sets[g * W + w] = cand_sets[c * W + w];
-            link[g] = ((uint64_t)(J.parent_off + p) << 8) | (uint64_t)a;
-            owner[g] = cand_owner[c];
-            table[cand_slot[c]] = (uint64_t)g;
-            ++rank;
+            link[g] = ((uint64_t)(J.parent_off + p) << 8) | (uint64_t)(local - p * J.k);
         }
+        table[cand_slot[c]] = (uint64_t)g;
+        ++rank;
     }
+}
+
+// Survivors per job: block_off at the job's last block minus at its first.
+__global__ void k_job_counts(const ExpandJob *__restrict__ jobs, int njobs, int64_t nblocks,
+                             const uint64_t *__restrict__ block_off, uint64_t *__restrict__ counts) {
+    int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= njobs) return;
+    int64_t b0 = jobs[j].cand_off / kScanBlock;
+    int64_t b1 = (j + 1 < njobs) ? jobs[j + 1].cand_off / kScanBlock : nblocks;
+    counts[j] = block_off[b1] - block_off[b0];
 }
 
 // ------------------------------------------------------------ meet check
@@ -549,14 +612,15 @@ template <int W, int NT>
 __global__ void __launch_bounds__(NT) k_meet_bm(const MeetJob *__restrict__ jobs, int njobs, int64_t ntiles,
                                                 int tf_rows, const uint64_t *__restrict__ sets,
                                                 unsigned long long *best, unsigned long long *pairs_done,
-                                                unsigned long long *and_iters) {
+                                                unsigned long long *and_iters,
+                                                unsigned long long *rows_transposed) {
     extern __shared__ __align__(16) uint32_t sT[];  // [64 W][kBmStride]
     __shared__ int64_t s_job;
     __shared__ int s_skip;
     __shared__ unsigned long long s_best;
     constexpr int NW = NT / 32;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    unsigned long long my_pairs = 0, my_iters = 0;
+    unsigned long long my_pairs = 0, my_iters = 0, my_rows = 0;
     for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
         if (threadIdx.x == 0) {
             int lo = 0, hi = njobs - 1;
@@ -581,6 +645,7 @@ __global__ void __launch_bounds__(NT) k_meet_bm(const MeetJob *__restrict__ jobs
         const int64_t f0 = tf * tf_rows;
         const int64_t f1 = min(f0 + tf_rows, J.f_cnt);
         // 1. transpose the backward chunk: group g = rows 32g..32g+31
+        my_rows += (unsigned long long)nb;
         for (int g = warp; g < kBmRows / 32; g += NW) {
             int row = g * 32 + lane;
             uint64_t y[W];
@@ -638,6 +703,7 @@ __global__ void __launch_bounds__(NT) k_meet_bm(const MeetJob *__restrict__ jobs
         if (my_pairs) atomicAdd(pairs_done, my_pairs);
         if (my_iters) atomicAdd(and_iters, my_iters);
     }
+    if (threadIdx.x == 0 && my_rows) atomicAdd(rows_transposed, my_rows);
 }
 
 // ------------------------------------------------------------ word recovery

@@ -62,7 +62,7 @@ def lib():
         L.sw_batch.restype = i32
         L.sw_batch_device.argtypes = [i32, p, p, p, p, p, p, sz, p, p, p, i64]
         L.sw_batch_device.restype = i32
-        L.sw_last_stats.argtypes = [p] * 12
+        L.sw_last_stats.argtypes = [p] * 13
         L.sw_last_stats.restype = i32
         L.sw_set_timing.argtypes = [i32]
         L.sw_set_timing.restype = None
@@ -70,6 +70,16 @@ def lib():
         L.sw_get_options.restype = None
         L.sw_set_options.argtypes = [p]
         L.sw_set_options.restype = None
+        L.sw_server_create.argtypes = [p, sz, i32, i32, i32, i32, p, p]
+        L.sw_server_create.restype = i32
+        L.sw_server_submit.argtypes = [p, p, ctypes.c_uint64]
+        L.sw_server_submit.restype = i32
+        L.sw_server_poll.argtypes = [p, p, p, p, i32, p]
+        L.sw_server_poll.restype = i32
+        L.sw_server_pending.argtypes = [p, p, p, p]
+        L.sw_server_pending.restype = i32
+        L.sw_server_destroy.argtypes = [p]
+        L.sw_server_destroy.restype = None
         _lib = L
     return _lib
 
@@ -192,16 +202,17 @@ def sw_batch_device(n, k, d_delta, delta_off, stream=None, ws=None, d_r=None, d_
 
 def sw_last_stats() -> dict:
     pairs, cand, launches, peak = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int64()
-    iters = ctypes.c_int64()
+    iters, rows = ctypes.c_int64(), ctypes.c_int64()
     it, ml, wv, ev = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32()
     mm, em, cm = ctypes.c_double(), ctypes.c_double(), ctypes.c_double()
     lib().sw_last_stats(ctypes.byref(pairs), ctypes.byref(cand), ctypes.byref(it), ctypes.byref(mm),
                         ctypes.byref(em), ctypes.byref(cm), ctypes.byref(ml), ctypes.byref(launches),
-                        ctypes.byref(wv), ctypes.byref(ev), ctypes.byref(peak), ctypes.byref(iters))
+                        ctypes.byref(wv), ctypes.byref(ev), ctypes.byref(peak), ctypes.byref(iters),
+                        ctypes.byref(rows))
     return {"pairs": pairs.value, "candidates": cand.value, "iterations": it.value, "meet_ms": mm.value,
             "expand_ms": em.value, "compact_ms": cm.value, "meet_launches": ml.value,
             "launches": launches.value, "waves": wv.value, "evictions": ev.value, "arena_peak": peak.value,
-            "and_iters": iters.value}
+            "and_iters": iters.value, "rows_transposed": rows.value}
 
 
 def sw_set_timing(on: bool) -> None:
@@ -216,3 +227,55 @@ def sw_get_options() -> sw_options:
 
 def sw_set_options(o: sw_options) -> None:
     lib().sw_set_options(ctypes.byref(o))
+
+
+class Server:
+    """sw_server_*: continuous batching of searches on one stream."""
+
+    def __init__(self, ws, n_max: int, k_max: int, max_requests: int = 4096, word_cap: int = 4096, stream=None):
+        self.ws = ws  # kept alive for the server's lifetime
+        self.word_cap = word_cap
+        self._word = np.zeros(word_cap, np.uint8)
+        srv = ctypes.c_void_p()
+        p, nb = _ws_args(ws)
+        rc = lib().sw_server_create(p, nb, n_max, k_max, max_requests, word_cap, _stream(stream),
+                                    ctypes.byref(srv))
+        if rc != SW_OK:
+            raise SwError(rc, "sw_server_create")
+        self.ptr = srv.value
+
+    def submit(self, h: Automaton, req_id: int) -> int:
+        """SW_OK, or SW_EBUSY when the submission queue is full."""
+        rc = lib().sw_server_submit(ctypes.c_void_p(self.ptr), ctypes.c_void_p(h.ptr), req_id)
+        if rc not in (SW_OK, SW_EBUSY):
+            raise SwError(rc, "sw_server_submit")
+        return rc
+
+    def poll(self):
+        """(req_id, r, word, code) of a finished request, or None."""
+        req = ctypes.c_uint64()
+        r = ctypes.c_int32()
+        code = ctypes.c_int32()
+        rc = lib().sw_server_poll(ctypes.c_void_p(self.ptr), ctypes.byref(req), ctypes.byref(r), _ptr(self._word),
+                                  self.word_cap, ctypes.byref(code))
+        if rc == SW_EAGAIN:
+            return None
+        if rc != SW_OK:
+            raise SwError(rc, "sw_server_poll")
+        word = self._word[: r.value].tolist() if code.value == SW_OK else None
+        return req.value, r.value, word, code.value
+
+    def pending(self):
+        q, a, f = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32()
+        rc = lib().sw_server_pending(ctypes.c_void_p(self.ptr), ctypes.byref(q), ctypes.byref(a), ctypes.byref(f))
+        if rc != SW_OK:
+            raise SwError(rc, "sw_server_pending")
+        return q.value, a.value, f.value
+
+    def close(self):
+        if getattr(self, "ptr", None):
+            lib().sw_server_destroy(ctypes.c_void_p(self.ptr))
+            self.ptr = None
+
+    def __del__(self):
+        self.close()

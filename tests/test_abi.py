@@ -78,7 +78,7 @@ def test_workspace_min_bytes(lib):
 
 def test_options_roundtrip(lib):
     o = sw.sw_get_options()
-    assert o.dir_theta == 1.0 and o.set_cost == 16384.0
+    assert o.dir_theta == 1.0 and o.set_cost == 8192.0 and o.meet_f_rows == 4096
     o.dir_theta = -3.0  # invalid: reset to the default
     sw.sw_set_options(o)
     assert sw.sw_get_options().dir_theta == 1.0

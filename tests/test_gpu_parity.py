@@ -187,3 +187,43 @@ def test_batch_device_not_synchronizing(sw, ws):
     assert rc == sw.SW_ENOTSYNC
     r = d_r.cpu().tolist()
     assert r[1] == -1 and r[0] == oracle.forward(good)[0]
+
+
+def test_server_results_equal_alone(sw):
+    """Requests arriving while others run are admitted into the running
+    iterations; each result equals the one computed alone."""
+    import time
+    rng = np.random.default_rng(77)
+    ds = []
+    for i in range(48):
+        n = int(rng.integers(16, 90))
+        k = int(rng.choice([2, 3, 4]))
+        ds.append(gen.random_automaton(n, k, 9000 + i))
+    ds.append(gen.cerny(12))
+    ds.append(np.zeros((2, 1), np.int32))
+    hs = [sw.load(d) for d in ds]
+    ws_alone = sw.workspace(256 << 20)
+    alone = [sw.sw_reset_threshold(h, ws=ws_alone) for h in hs]
+    srv = sw.Server(sw.workspace(1 << 30), n_max=128, k_max=4, max_requests=64)
+    got = {}
+    try:
+        for i, h in enumerate(hs):  # staggered arrivals
+            while srv.submit(h, i) == sw.SW_EBUSY:
+                time.sleep(0.001)
+            if i % 5 == 0:
+                time.sleep(0.002)
+            while (res := srv.poll()) is not None:
+                got[res[0]] = res
+        t0 = time.time()
+        while len(got) < len(hs) and time.time() - t0 < 120:
+            res = srv.poll()
+            if res is None:
+                time.sleep(0.001)
+            else:
+                got[res[0]] = res
+    finally:
+        srv.close()
+    assert len(got) == len(hs)
+    for i in range(len(hs)):
+        req, r, w, code = got[i]
+        assert code == 0 and (r, w) == alone[i], i
