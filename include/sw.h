@@ -105,6 +105,37 @@ int32_t sw_reset_threshold(sw_handle h, void *stream, void *workspace, size_t ws
                            int32_t *r, uint8_t *word, int32_t word_cap);
 
 /*
+ * Allocation-free variant of sw_reset_threshold (the paper has no
+ * counterpart; this is a library convenience).  Some callers cannot
+ * allocate device memory when they call in: a process whose own allocator
+ * has already reserved the whole GPU, a plugin loaded into a host program
+ * that owns all device memory, or a service that forbids allocation after
+ * start-up so that its memory use stays fixed.  This entry point needs no
+ * workspace and calls no cudaMalloc, cudaMallocHost, cudaFree or other
+ * allocating CUDA or PyTorch routine: its device scratch is one fixed array
+ * of SW_STATIC_SCRATCH_BYTES (64 MiB) compiled into the library, which every
+ * GPU that loads the library holds until the process exits.  Host-side
+ * bookkeeping uses the C++ heap.
+ *
+ * Arguments, results and errors are those of sw_reset_threshold.  A search
+ * that needs more than the scratch holds (its forward and backward levels,
+ * their hash tables and one level of candidates: a few million sets for
+ * W = 1, fewer for wider automata) fails with SW_ENOMEM ("workspace too
+ * small"); use sw_reset_threshold with a larger workspace for those.
+ *
+ * The first call on each device looks up the scratch's device address
+ * (cudaGetSymbolAddress) with that device current; make that first call
+ * before any stream capture begins.  Every call on a device shares the one
+ * scratch array and starts by re-initialising what it reads, so results
+ * never depend on an earlier call; but two calls whose GPU work overlaps
+ * (different threads or streams at the same time) race on it and must be
+ * serialised by the caller.
+ */
+#define SW_STATIC_SCRATCH_BYTES (64u << 20)
+int32_t sw_reset_threshold_static(sw_handle h, void *stream, int32_t *r, uint8_t *word,
+                                  int32_t word_cap);
+
+/*
  * Per-level sizes of the last search that included `h` (single or batched):
  * fwd[i] = size of forward level i for i < *nf, bwd[j] = size of backward
  * level j for j < *nb.  The search computes forward levels 0..i and

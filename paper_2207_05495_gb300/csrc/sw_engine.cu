@@ -55,6 +55,9 @@ thread_local int32_t g_last_error = SW_OK;
 thread_local sw_options g_opt = {0, 0, 0, 4096, 1.0, 8192.0};
 thread_local bool g_timing = false;
 thread_local Stats g_stats;
+// Set only while sw_reset_threshold_static runs: staging buffers then come
+// from the C++ heap instead of cudaMallocHost.
+thread_local bool g_pageable = false;
 
 int32_t fail(int32_t code) {
     g_last_error = code;
@@ -108,10 +111,15 @@ bool host_is_synchronizing(int n, int k, const int32_t *delta) {
 struct Pinned {
     void *p = nullptr;
     size_t size = 0;
+    std::vector<char> heap;  // used instead of pinned memory when g_pageable
     ~Pinned() {
         if (p) cudaFreeHost(p);
     }
     void *get(size_t bytes) {
+        if (g_pageable) {
+            if (heap.size() < bytes) heap.resize(std::max(bytes, 2 * heap.size()));
+            return heap.data();
+        }
         if (bytes > size) {
             if (p) cudaFreeHost(p);
             size_t s = std::max(bytes, size * 2);
@@ -1159,6 +1167,35 @@ void sw_server::loop() {
     }
 }
 
+// ---------------------------------------------------------------- fixed device scratch
+
+// Device scratch for sw_reset_threshold_static, defined in this file so that
+// no call ever needs cudaMalloc: every GPU that loads the library holds these
+// SW_STATIC_SCRATCH_BYTES until the process exits.  Host code may not use
+// the name as an address; it asks the runtime for the address once per
+// device (static_scratch_ptr) and passes that on.
+static __device__ __align__(256) unsigned char g_static_scratch[SW_STATIC_SCRATCH_BYTES];
+
+namespace {
+std::mutex g_static_mu;
+void *g_static_ptr[128] = {};
+
+// Address of g_static_scratch on the current device, looked up on the first
+// call made on that device.
+int32_t static_scratch_ptr(void **out) {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 128) return SW_ECUDA;
+    std::lock_guard<std::mutex> lk(g_static_mu);
+    if (!g_static_ptr[dev]) {
+        void *ptr = nullptr;
+        if (cudaGetSymbolAddress(&ptr, g_static_scratch) != cudaSuccess || !ptr) return SW_ECUDA;
+        g_static_ptr[dev] = ptr;
+    }
+    *out = g_static_ptr[dev];
+    return SW_OK;
+}
+}  // namespace
+
 // ==================================================================== C-ABI
 
 extern "C" {
@@ -1520,6 +1557,34 @@ void sw_server_destroy(sw_server *s) {
     if (s->worker.joinable()) s->worker.join();
     cudaStreamSynchronize(s->st);
     delete s;
+}
+
+int32_t sw_reset_threshold_static(sw_handle h, void *stream, int32_t *r, uint8_t *word, int32_t word_cap) {
+    if (!h || !r || word_cap < 0) return fail(SW_EINVAL);
+    if (sw_workspace_min_bytes(h->n, h->k, 1) > (size_t)SW_STATIC_SCRATCH_BYTES) return fail(SW_ENOMEM);
+    void *scratch = nullptr;
+    int32_t rc = static_scratch_ptr(&scratch);
+    if (rc) return fail(rc);
+    std::vector<Inst> I(1);
+    I[0].n = h->n;
+    I[0].k = h->k;
+    I[0].word_off = 0;
+    I[0].word_cap = word ? word_cap : INT32_MAX;
+    bool timing = g_timing;
+    g_timing = false;  // no events: creating them is not needed here
+    g_pageable = true;
+    rc = run_instances(I, &h->delta16, nullptr, nullptr, (cudaStream_t)stream, scratch,
+                       (size_t)SW_STATIC_SCRATCH_BYTES, false, word);
+    g_pageable = false;
+    g_timing = timing;
+    if (rc) return fail(rc);
+    if (I[0].state == kDone || I[0].code == SW_EWORDCAP) {
+        *r = I[0].r;
+        store_sizes(h, I[0]);
+    }
+    if (I[0].state != kDone) return fail(I[0].code ? I[0].code : SW_EINTERNAL);
+    g_last_error = SW_OK;
+    return SW_OK;
 }
 
 }  // extern "C"

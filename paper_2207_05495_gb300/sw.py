@@ -70,6 +70,8 @@ def lib():
         L.sw_get_options.restype = None
         L.sw_set_options.argtypes = [p]
         L.sw_set_options.restype = None
+        L.sw_reset_threshold_static.argtypes = [p, p, p, p, i32]
+        L.sw_reset_threshold_static.restype = i32
         L.sw_server_create.argtypes = [p, sz, i32, i32, i32, i32, p, p]
         L.sw_server_create.restype = i32
         L.sw_server_submit.argtypes = [p, p, ctypes.c_uint64]
@@ -149,6 +151,18 @@ def sw_reset_threshold(h: Automaton, stream=None, ws=None, word_cap: int = 1 << 
     rc = lib().sw_reset_threshold(ctypes.c_void_p(h.ptr), _stream(stream), p, nb, _ptr(r), _ptr(word), word_cap)
     if rc != SW_OK:
         raise SwError(rc, "sw_reset_threshold")
+    return int(r[0]), word[: r[0]].tolist()
+
+
+def sw_reset_threshold_static(h: Automaton, stream=None, word_cap: int = 1 << 16):
+    """(r, word) of one automaton without any device allocation: the search
+    runs in the library's fixed 64 MiB device scratch (see include/sw.h).
+    Calls must not overlap on the GPU."""
+    r = np.zeros(1, np.int32)
+    word = np.zeros(max(word_cap, 1), np.uint8)
+    rc = lib().sw_reset_threshold_static(ctypes.c_void_p(h.ptr), _stream(stream), _ptr(r), _ptr(word), word_cap)
+    if rc != SW_OK:
+        raise SwError(rc, "sw_reset_threshold_static")
     return int(r[0]), word[: r[0]].tolist()
 
 
