@@ -10,8 +10,9 @@ least shortest reset word of every instance.
   e2e           the same through sw_batch with host buffers (automata copied
                 in and results copied out inside the timed region).
   roofline      the meet kernel (the dominant kernel), integer-ALU bound:
-                int32 operations it performs (64 per warp-wide 64-bit AND
-                step, 25 per 32-bit word of each transposed backward row)
+                int32 operations it performs (64 per 64-bit lane word of a
+                warp-wide AND step, 25 per 32-bit word of each transposed
+                backward row)
                 against 128 int32 lanes/SM x SMs x maximum SM clock.
   serving       sw_server under Poisson arrivals (n~U[32,128], k in 2..4)
                 at 0.8x the batched capacity: p50/p99 latency, instances/s.
@@ -49,10 +50,24 @@ SM_MAX_MHZ_FALLBACK = 2070.0
 N_SMS_NOMINAL = 152
 
 
+def rank_seeds(rank: int, count: int) -> range:
+    """Weak scaling: rank r solves its own `count` automata, seeds
+    r*count .. (r+1)*count - 1 (no data exchange between ranks)."""
+    return range(rank * count, (rank + 1) * count)
+
+
+def max_over_ranks(x: float, dist, device) -> float:
+    """The job's time is the slowest rank's."""
+    import torch
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
 def workload(name: str, rank: int = 0):
     if name == "c3":
         count = 4096
-        seeds = range(rank * count, (rank + 1) * count)
+        seeds = rank_seeds(rank, count)
         return [gen.random_automaton_ranged(64, 192, 2, s) for s in seeds], {
             "workload": "batch of 4096 random binary automata, n~U[64,192], k=2, seeds 0..4095, 3x64-bit bitsets",
             "instances": count, "n_range": [64, 192], "k": 2}
@@ -301,6 +316,9 @@ def main():
             dist.barrier()
 
     count = len(ds)
+    from paper_2207_05495_gb300 import autotune
+    tuned = autotune.apply(max((d.shape[1] + 63) // 64 for d in ds), int(ds[0].shape[0]))
+    cfg["options"] = tuned if tuned else "library defaults"
     ns = np.array([d.shape[1] for d in ds], np.int32)
     ks = np.array([d.shape[0] for d in ds], np.int32)
     W = int(max((int(n) + 63) // 64 for n in ns))
@@ -345,9 +363,7 @@ def main():
     sw.sw_set_timing(False)
     ms = float(np.mean(times))
     if world > 1:
-        t = torch.tensor([ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+        ms = max_over_ranks(ms, dist, "cuda")
     value = count * world / (ms * 1e-3)
 
     # results of the last timed step, checked: every word resets Q
@@ -396,8 +412,9 @@ def main():
     iters = sum(s["and_iters"] for s in stats) / len(stats)
     rows_t = sum(s["rows_transposed"] for s in stats) / len(stats)
     launches = sum(s["meet_launches"] for s in stats) / len(stats)
-    ops = iters * 64 + rows_t * 2 * W * 25
-    smem_bytes = iters * 256 + rows_t * 8 * W
+    lw = 2 if W <= 3 else 1  # 64-bit words of the running AND per lane
+    ops = iters * 64 * lw + rows_t * 2 * W * 25
+    smem_bytes = iters * 256 * lw + rows_t * 8 * W
     sec = meet_ms * 1e-3
     achieved = ops / sec / 1e12 if sec > 0 else 0.0
     props = torch.cuda.get_device_properties(local)
@@ -414,7 +431,7 @@ def main():
                 "d2h_bytes_per_step": d2h},
         "roofline": {"bound": "alu", "kernel": "k_meet_bm", "achieved": achieved, "peak": peak, "unit": "Tops/s",
                      "frac": achieved / peak if peak else None, "traffic": None,
-                     "work": "int32 ops executed: 64 per warp AND step + 25 per transposed 32-bit row word",
+                     "work": "int32 ops executed: 64 per 64-bit lane word per warp AND step + 25 per transposed 32-bit row word",
                      "and_steps_per_step": iters, "rows_transposed_per_step": rows_t,
                      "smem_tbs": smem_bytes / sec / 1e12 if sec > 0 else 0.0, "smem_peak_tbs": smem_peak,
                      "pairs_per_step": pairs, "pairs_per_sec_in_kernel": pairs / sec if sec > 0 else 0.0,

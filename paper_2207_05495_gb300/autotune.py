@@ -1,0 +1,125 @@
+"""Autotuner for the search's tunable parameters (sw_options).
+
+It times the batched search on a sample of automata for every candidate
+setting of the meet kernel's forward rows per tile and of the direction
+rule (SetCost and the threshold theta of the step-cost comparison,
+Section 2.1.2), requires every candidate to return identical r and words,
+and keeps the fastest.  Results are cached in tuned.json next to this file,
+keyed by (words per set W, letters k, GPU name); `apply` loads the entry for
+a workload into the calling thread's options.
+
+    python -m paper_2207_05495_gb300.autotune   # tunes the 4096-automaton workload's shape
+"""
+
+from __future__ import annotations
+
+import itertools
+import json
+import os
+import time
+
+import numpy as np
+
+from . import gen, sw
+
+CACHE = os.path.join(os.path.dirname(os.path.abspath(__file__)), "tuned.json")
+
+GRID = {
+    "meet_f_rows": [1024, 4096, 16384],
+    "set_cost": [2048.0, 8192.0, 32768.0],
+    "dir_theta": [0.5, 1.0, 2.0],
+}
+
+
+def key(W: int, k: int, gpu: str) -> str:
+    return f"W{W}-k{k}-{gpu}"
+
+
+def _gpu_name() -> str:
+    import torch
+    return torch.cuda.get_device_name(0)
+
+
+def tune(automata, ws, grid=None, repeats: int = 2, verbose: bool = False) -> dict:
+    """Times sw_batch over `automata` for every combination in `grid`
+    (dict of option name -> values); returns {"best": {...}, "trials": [...]}."""
+    import torch
+    grid = grid or GRID
+    hs = [sw.load(d) for d in automata]
+    base = sw.sw_get_options()
+    names = list(grid)
+    ref = None
+    trials = []
+    try:
+        for combo in itertools.product(*(grid[n] for n in names)):
+            o = sw.sw_get_options()
+            for n, v in zip(names, combo):
+                setattr(o, n, v)
+            sw.sw_set_options(o)
+            sw.sw_batch(hs[: max(1, len(hs) // 8)], ws=ws)  # warm
+            best_t = None
+            for _ in range(repeats):
+                torch.cuda.synchronize()
+                t0 = time.perf_counter()
+                r, w = sw.sw_batch(hs, ws=ws)
+                torch.cuda.synchronize()
+                t = time.perf_counter() - t0
+                best_t = t if best_t is None else min(best_t, t)
+            if ref is None:
+                ref = (r.copy(), w)
+            elif not ((r == ref[0]).all() and w == ref[1]):
+                raise RuntimeError(f"setting {dict(zip(names, combo))} changed the results")
+            trial = dict(zip(names, combo))
+            trial["seconds"] = best_t
+            trials.append(trial)
+            if verbose:
+                print(trial, flush=True)
+    finally:
+        sw.sw_set_options(base)
+    best = min(trials, key=lambda t: t["seconds"])
+    return {"best": {n: best[n] for n in names}, "seconds": best["seconds"], "trials": trials}
+
+
+def load_cache() -> dict:
+    if os.path.exists(CACHE):
+        with open(CACHE) as fh:
+            return json.load(fh)
+    return {}
+
+
+def save(entry_key: str, result: dict) -> None:
+    cache = load_cache()
+    cache[entry_key] = {"options": result["best"], "seconds": result["seconds"],
+                        "when": time.strftime("%Y-%m-%dT%H:%M:%SZ", time.gmtime())}
+    with open(CACHE, "w") as fh:
+        json.dump(cache, fh, indent=1, sort_keys=True)
+
+
+def apply(W: int, k: int) -> dict | None:
+    """Sets the calling thread's options from the cache entry for (W, k, this
+    GPU); returns the options applied, or None when there is no entry."""
+    entry = load_cache().get(key(W, k, _gpu_name()))
+    if not entry:
+        return None
+    o = sw.sw_get_options()
+    for n, v in entry["options"].items():
+        setattr(o, n, type(getattr(o, n))(v))
+    sw.sw_set_options(o)
+    return entry["options"]
+
+
+def main():
+    import torch
+    from . import build
+    build.build()
+    torch.cuda.set_device(0)
+    sample = gen.batch_random(512, 64, 192, 2, 0)
+    W = max((d.shape[1] + 63) // 64 for d in sample)
+    ws = sw.workspace(96 << 30)
+    res = tune(sample, ws, verbose=True)
+    save(key(W, 2, _gpu_name()), res)
+    print(json.dumps({"key": key(W, 2, _gpu_name()), "best": res["best"], "seconds": res["seconds"]}))
+
+
+if __name__ == "__main__":
+    main()

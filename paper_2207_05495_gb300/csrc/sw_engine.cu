@@ -382,7 +382,7 @@ MeetCfg meet_cfg(int W) {
     c.tb = std::min(tb, max_tb);
     c.nt = 256;
     c.algo = g_opt.meet_algo == 1 ? 1 : 0;
-    if (c.algo == 0) c.tb = kBmRows;
+    if (c.algo == 0) c.tb = bm_rows(W);
     c.tf_rows = g_opt.meet_f_rows > 0 ? g_opt.meet_f_rows : 4096;
     c.tf_rows = std::max(8, std::min(c.tf_rows, 1 << 20));
     return c;
@@ -412,9 +412,9 @@ template <int W>
 cudaError_t launch_meet_bm(const MeetJob *jobs, int njobs, int64_t ntiles, int tf_rows, const uint64_t *sets,
                            unsigned long long *best, unsigned long long *pairs, unsigned long long *iters,
                            unsigned long long *rows, cudaStream_t st) {
-    constexpr int NT = 256;
+    constexpr int NT = kBmThreads;
     auto kern = k_meet_bm<W, NT>;
-    size_t smem = (size_t)64 * W * kBmStride * sizeof(uint32_t);
+    size_t smem = (size_t)bm_smem_bytes(W);
     static thread_local bool configured = false;
     if (!configured) {
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);

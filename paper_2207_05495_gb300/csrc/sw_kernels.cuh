@@ -578,22 +578,36 @@ __global__ void __launch_bounds__(NT) k_meet(const MeetJob *__restrict__ jobs, i
     if (threadIdx.x == 0 && my_pairs) atomicAdd(pairs_done, my_pairs);
 }
 
-// Meet check by vertical bitmaps.  A backward chunk of up to 2048 sets
-// B[b0 .. b0+2047] is transposed into shared memory as one bitmap per state:
+// Meet check by vertical bitmaps.  A backward chunk of up to kBmRows(LW)
+// sets B[b0 ..] is transposed into shared memory as one bitmap per state:
 // bit b of M_q is set iff state q lies in B[b0 + b].  Then X is inside
 // B[b0 + b] iff bit b survives the AND of M_q over the states q of X.  A
-// warp takes one forward set X at a time; lane l holds bits 64l..64l+63 of
-// the running AND and the warp stops as soon as every lane is zero (after
-// about five states of X on random instances, against 2W LOP3 per pair for
-// the direct test).  Rows of F are taken in increasing order, so the first
+// warp takes one forward set X at a time; lane l holds 64*LW bits of the
+// running AND and the warp stops as soon as every lane is zero (after about
+// five states of X on random instances, against 2W LOP3 per pair for the
+// direct test).  Rows of F are taken in increasing order, so the first
 // survivor of a warp is its least meeting f; a tile whose first row lies
 // beyond the best f found so far is skipped.
 //
-// Shared layout: 32-bit words, M_q's word g (rows 32g..32g+31) at
-// sT[q * kBmStride + g]; the stride 66 keeps the transposing stores at most
-// 2-way bank conflicted and the 64-bit loads of the AND loop aligned.
-constexpr int kBmRows = 2048;   // backward sets per chunk
-constexpr int kBmStride = 66;   // 32-bit words per state row (64 used)
+// Shared layout: M_q occupies kBmWords(LW) 32-bit words; lane l's 2*LW
+// words (rows 64*LW*l ..) sit at unit (l ^ (q & 31)) of the row, so that
+// the AND loop's 8- or 16-byte loads are aligned and conflict-free and the
+// transposing stores are at most 2*LW-way conflicted.
+template <int LW>
+struct Bm {
+    static constexpr int kRows = 2048 * LW;  // backward sets per chunk
+    static constexpr int kWords = 64 * LW;   // 32-bit words per state bitmap
+    static constexpr int kUnit = 2 * LW;     // 32-bit words per lane
+    __device__ static __forceinline__ int pos(int q, int g) {
+        return q * kWords + (((g / kUnit) ^ (q & 31)) * kUnit) + (g % kUnit);
+    }
+};
+
+// Backward rows per chunk for W words per set (host and device).
+__host__ __device__ constexpr int bm_lanes_words(int W) { return W <= 3 ? 2 : 1; }
+__host__ __device__ constexpr int bm_rows(int W) { return 2048 * bm_lanes_words(W); }
+__host__ __device__ constexpr int bm_smem_bytes(int W) { return 64 * W * 64 * bm_lanes_words(W) * 4; }
+constexpr int kBmThreads = 512;
 
 // 32x32 bit transpose across a warp: lane j holds row j on entry (bit i =
 // entry (j, i)); on exit lane i holds column i (bit j = entry (j, i)).
@@ -614,7 +628,9 @@ __global__ void __launch_bounds__(NT) k_meet_bm(const MeetJob *__restrict__ jobs
                                                 unsigned long long *best, unsigned long long *pairs_done,
                                                 unsigned long long *and_iters,
                                                 unsigned long long *rows_transposed) {
-    extern __shared__ __align__(16) uint32_t sT[];  // [64 W][kBmStride]
+    constexpr int LW = bm_lanes_words(W);
+    using G = Bm<LW>;
+    extern __shared__ __align__(16) uint32_t sT[];  // [64 W][G::kWords]
     __shared__ int64_t s_job;
     __shared__ int s_skip;
     __shared__ unsigned long long s_best;
@@ -640,13 +656,13 @@ __global__ void __launch_bounds__(NT) k_meet_bm(const MeetJob *__restrict__ jobs
         const MeetJob &J = jobs[s_job];
         const int64_t local = tile - J.tile_off;
         const int64_t tf = local / J.ntb;
-        const int64_t b0 = (local - tf * J.ntb) * kBmRows;
-        const int nb = (int)min((int64_t)kBmRows, J.b_cnt - b0);
+        const int64_t b0 = (local - tf * J.ntb) * G::kRows;
+        const int nb = (int)min((int64_t)G::kRows, J.b_cnt - b0);
         const int64_t f0 = tf * tf_rows;
         const int64_t f1 = min(f0 + tf_rows, J.f_cnt);
         // 1. transpose the backward chunk: group g = rows 32g..32g+31
         my_rows += (unsigned long long)nb;
-        for (int g = warp; g < kBmRows / 32; g += NW) {
+        for (int g = warp; g < G::kRows / 32; g += NW) {
             int row = g * 32 + lane;
             uint64_t y[W];
             if (row < nb) load_set<W>(sets + (J.b_off + b0 + row) * W, y);
@@ -658,43 +674,73 @@ __global__ void __launch_bounds__(NT) k_meet_bm(const MeetJob *__restrict__ jobs
             for (int h = 0; h < 2 * W; ++h) {
                 uint32_t v = (h & 1) ? (uint32_t)(y[h >> 1] >> 32) : (uint32_t)y[h >> 1];
                 uint32_t c = warp_transpose32(v, lane);  // column lane: state 32h + lane
-                sT[(32 * h + lane) * kBmStride + g] = c;
+                sT[G::pos(32 * h + lane, g)] = c;
             }
         }
         __syncthreads();
         // 2. forward rows, one per warp at a time, in increasing order
-        const int lim = nb - 64 * lane;
-        const uint64_t lane_mask = lim >= 64 ? ~0ull : (lim > 0 ? ((1ull << lim) - 1) : 0ull);
-        for (int64_t f = f0 + warp; f < f1; f += NW) {
+        uint64_t mask[LW];
+#pragma unroll
+        for (int j = 0; j < LW; ++j) {
+            int lim = nb - 64 * (LW * lane + j);
+            mask[j] = lim >= 64 ? ~0ull : (lim > 0 ? ((1ull << lim) - 1) : 0ull);
+        }
+        int64_t f = f0 + warp;
+        uint64_t x[W];
+        if (f < f1) load_set<W>(sets + (J.f_off + f) * W, x);
+        for (; f < f1; f += NW) {
             // lane 0 reads the shared best; the whole warp follows its decision
             int stop = (int64_t)(*(volatile unsigned long long *)&s_best >> 32) < f;
             if (__shfl_sync(0xffffffffu, stop, 0)) break;
-            uint64_t x[W];
-            load_set<W>(sets + (J.f_off + f) * W, x);
-            uint64_t acc = lane_mask;
+            uint64_t xn[W];  // prefetch the warp's next row
+            if (f + NW < f1) load_set<W>(sets + (J.f_off + f + NW) * W, xn);
+            uint64_t acc[LW];
+#pragma unroll
+            for (int j = 0; j < LW; ++j) acc[j] = mask[j];
             bool alive = true;
 #pragma unroll
-            for (int w = 0; w < W; ++w) {
-                uint64_t bits = x[w];
+            for (int h = 0; h < 2 * W; ++h) {
+                uint32_t bits = (h & 1) ? (uint32_t)(x[h >> 1] >> 32) : (uint32_t)x[h >> 1];
                 while (bits && alive) {
-                    int q = w * 64 + __ffsll((long long)bits) - 1;
+                    const int q = 32 * h + __ffs(bits) - 1;
                     bits &= bits - 1;
-                    acc &= *reinterpret_cast<const uint64_t *>(sT + q * kBmStride + 2 * lane);
+                    const uint32_t *p = sT + q * G::kWords + ((lane ^ (q & 31)) * G::kUnit);
+                    uint64_t any;
+                    if constexpr (LW == 2) {
+                        uint4 v = *reinterpret_cast<const uint4 *>(p);
+                        acc[0] &= ((uint64_t)v.y << 32) | v.x;
+                        acc[LW - 1] &= ((uint64_t)v.w << 32) | v.z;
+                        any = acc[0] | acc[LW - 1];
+                    } else {
+                        uint2 v = *reinterpret_cast<const uint2 *>(p);
+                        acc[0] &= ((uint64_t)v.y << 32) | v.x;
+                        any = acc[0];
+                    }
                     ++my_iters;
-                    alive = __any_sync(0xffffffffu, acc != 0);
+                    alive = __any_sync(0xffffffffu, any != 0);
                 }
             }
             my_pairs += (unsigned long long)nb;
             if (alive) {  // every state of X processed: X lies inside the surviving sets
-                unsigned ball = __ballot_sync(0xffffffffu, acc != 0);
+                uint64_t any = 0;
+#pragma unroll
+                for (int j = 0; j < LW; ++j) any |= acc[j];
+                unsigned ball = __ballot_sync(0xffffffffu, any != 0);
                 if (lane == __ffs(ball) - 1) {
-                    unsigned long long key = ((unsigned long long)f << 32) |
-                                             (unsigned long long)(b0 + 64 * lane + __ffsll((long long)acc) - 1);
+                    int j = 0;
+#pragma unroll
+                    for (int t = LW - 1; t >= 0; --t)
+                        if (acc[t]) j = t;
+                    unsigned long long key =
+                        ((unsigned long long)f << 32) |
+                        (unsigned long long)(b0 + 64 * (LW * lane + j) + __ffsll((long long)acc[j]) - 1);
                     atomicMin(&s_best, key);
                     atomicMin(best + J.slot, key);
                 }
                 break;  // later rows of this warp cannot give a smaller f
             }
+#pragma unroll
+            for (int w = 0; w < W; ++w) x[w] = xn[w];
         }
         __syncthreads();
     }
