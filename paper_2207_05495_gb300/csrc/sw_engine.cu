@@ -203,6 +203,7 @@ struct Inst {
     int64_t delta_off = 0;
     std::vector<Level> lev[2];
     int64_t tab_off[2] = {-1, -1}, tab_cap[2] = {0, 0}, stored[2] = {0, 0};
+    int64_t ge_off = -1;  // cardinality table of the current backward level (-1: B_0)
     double dupl[2] = {0.0, 0.0};
     int32_t state = kWaiting, code = SW_OK, r = -1;
     int32_t evictions = 0;
@@ -233,6 +234,9 @@ struct Layout {
     int64_t word_area_cap;
     uint16_t *delta16;
     int64_t delta_cap;
+    uint32_t *hist, *cursor;  // per job: survivor cardinalities, bucket cursors
+    int32_t *meta;            // pool of backward levels' cardinality tables
+    int64_t cap_meta;
     // pools
     uint64_t *sets, *link;
     int64_t cap_sets;
@@ -268,7 +272,9 @@ struct Carver {
 size_t mirror_bytes_for(int32_t count) { return (size_t)std::max(count, 1) * 1024 + (1 << 20); }
 int64_t word_area_for(int32_t count) { return (int64_t)std::max<size_t>((size_t)std::max(count, 1) * 512, 1 << 20); }
 
-size_t small_area_bytes(int32_t count, int64_t delta_elems) {
+int64_t meta_cap_for(int32_t count, int W) { return (int64_t)(2 * std::max(count, 1) + 64) * card_slots(W); }
+
+size_t small_area_bytes(int32_t count, int64_t delta_elems, int W = 9) {
     size_t c = (size_t)std::max(count, 1);
     size_t b = 0;
     auto add = [&](size_t x) { b += (x + 255) & ~(size_t)255; };
@@ -280,6 +286,8 @@ size_t small_area_bytes(int32_t count, int64_t delta_elems) {
     add(3 * sizeof(unsigned long long));
     add((size_t)word_area_for(count));
     add((size_t)std::max<int64_t>(delta_elems, 1) * sizeof(uint16_t));
+    add(2 * c * card_slots(W) * sizeof(uint32_t));
+    add((size_t)meta_cap_for(count, W) * sizeof(int32_t));
     return b;
 }
 
@@ -299,6 +307,10 @@ bool carve(void *ws, size_t bytes, int W, int32_t count, int64_t delta_elems, La
     L.word_area = cv.take<uint8_t>((size_t)L.word_area_cap);
     L.delta_cap = std::max<int64_t>(delta_elems, 1);
     L.delta16 = cv.take<uint16_t>((size_t)L.delta_cap);
+    L.hist = cv.take<uint32_t>(c * card_slots(W));
+    L.cursor = cv.take<uint32_t>(c * card_slots(W));
+    L.cap_meta = meta_cap_for(count, W);
+    L.meta = cv.take<int32_t>((size_t)L.cap_meta);
     if (!cv.ok) return false;
     size_t rest = cv.size - cv.used;
     if (rest < 256 * 1024) return false;
@@ -411,7 +423,7 @@ cudaError_t launch_meet_r(const MeetJob *jobs, int njobs, int64_t ntiles, int tb
 template <int W>
 cudaError_t launch_meet_bm(const MeetJob *jobs, int njobs, int64_t ntiles, int tf_rows, const uint64_t *sets,
                            unsigned long long *best, unsigned long long *pairs, unsigned long long *iters,
-                           unsigned long long *rows, cudaStream_t st) {
+                           unsigned long long *rows, const int32_t *meta, cudaStream_t st) {
     constexpr int NT = kBmThreads;
     auto kern = k_meet_bm<W, NT>;
     size_t smem = (size_t)bm_smem_bytes(W);
@@ -424,7 +436,7 @@ cudaError_t launch_meet_bm(const MeetJob *jobs, int njobs, int64_t ntiles, int t
     int per_sm = 0;
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, NT, smem);
     int64_t grid = std::min<int64_t>((int64_t)sm_count() * std::max(per_sm, 1), ntiles);
-    kern<<<(unsigned)grid, NT, smem, st>>>(jobs, njobs, ntiles, tf_rows, sets, best, pairs, iters, rows);
+    kern<<<(unsigned)grid, NT, smem, st>>>(jobs, njobs, ntiles, tf_rows, sets, best, pairs, iters, rows, meta);
     return cudaGetLastError();
 }
 
@@ -462,11 +474,16 @@ struct Ops {
     }
     static cudaError_t compact(const ExpandJob *jobs, int nj, int64_t ncand, const Layout &L, cudaStream_t st) {
         int64_t nblocks = ncand / kScanBlock;
-        g_stats.launches += 4;
-        k_flag_count<<<(unsigned)nblocks, kScanThreads, 0, st>>>(ncand, L.cand_slot, L.table, L.flag, L.block_cnt);
+        constexpr int HN = card_slots(W);
+        g_stats.launches += 5;
+        cudaError_t e = cudaMemsetAsync(L.hist, 0, (size_t)nj * HN * sizeof(uint32_t), st);
+        if (e != cudaSuccess) return e;
+        k_flag_count<W><<<(unsigned)nblocks, kScanThreads, 0, st>>>(jobs, nj, ncand, L.cand_slot, L.table,
+                                                                    L.cand_sets, L.flag, L.block_cnt, L.hist);
         k_scan_blocks<<<1, 1024, 0, st>>>(nblocks, L.block_cnt, L.block_off);
+        k_ge<<<(unsigned)nj, 32, 0, st>>>(jobs, HN, L.hist, L.cursor, L.meta);
         k_compact<W><<<(unsigned)nblocks, kScanThreads, 0, st>>>(jobs, nj, ncand, L.flag, L.block_off, L.cand_sets,
-                                                                 L.cand_slot, L.table, L.sets, L.link);
+                                                                 L.cand_slot, L.table, L.sets, L.link, L.cursor);
         k_job_counts<<<(unsigned)((nj + 255) / 256), 256, 0, st>>>(jobs, nj, nblocks, L.block_off, L.counts);
         return cudaGetLastError();
     }
@@ -475,7 +492,7 @@ struct Ops {
         g_stats.launches++;
         if (c.algo == 0)
             return launch_meet_bm<W>(jobs, nj, ntiles, c.tf_rows, L.sets, L.best, L.pairs, L.pairs + 1, L.pairs + 2,
-                                     st);
+                                     L.meta, st);
         switch (c.R) {
             case 1:
                 if constexpr (W >= 3) return launch_meet_r<W, 1>(jobs, nj, ntiles, c.tb, L.sets, L.best, L.pairs, st);
@@ -570,7 +587,7 @@ struct Engine {
     Layout L;
     OpTable ops;
     MeetCfg mc;
-    Pool set_pool, tab_pool;
+    Pool set_pool, tab_pool, meta_pool;
     std::vector<Inst> &I;
     bool device_words = false;  // words go straight to the caller's device buffer
     uint8_t *out_words = nullptr;
@@ -582,6 +599,7 @@ struct Engine {
         mc = meet_cfg(W);
         set_pool.init(L.cap_sets);
         tab_pool.init(L.cap_table);
+        meta_pool.init(L.cap_meta);
     }
 
     bool stage_begin() {
@@ -614,6 +632,8 @@ struct Engine {
             x.tab_cap[d] = 0;
             x.stored[d] = 0;
         }
+        if (x.ge_off >= 0) meta_pool.release(x.ge_off, card_slots(W));
+        x.ge_off = -1;
     }
 
     void finish(Inst &x, int state, int code) {
@@ -694,7 +714,7 @@ struct Engine {
         if (!stage_begin()) return SW_ECUDA;
         struct Sel {
             int id, d;
-            int64_t nc, dest, new_tab, new_cap;
+            int64_t nc, dest, new_tab, new_cap, ge;
         };
         std::vector<Sel> sel;
         int64_t ncand = 0;
@@ -718,6 +738,14 @@ struct Engine {
                 if (nt < 0) continue;
             }
             int64_t dest = set_pool.alloc(nc);
+            int64_t ge = -1;
+            if (dest >= 0 && d == 1) {
+                ge = meta_pool.alloc(card_slots(W));
+                if (ge < 0) {
+                    set_pool.release(dest, nc);
+                    dest = -1;
+                }
+            }
             if (dest < 0) {
                 if (nt >= 0) tab_pool.release(nt, ntc);
                 continue;
@@ -728,7 +756,7 @@ struct Engine {
                 x.tab_cap[d] = ntc;
                 seg_count += segs_here;
             }
-            sel.push_back({id, d, nc, dest, nt, ntc});
+            sel.push_back({id, d, nc, dest, nt, ntc, ge});
             ncand += ncp;
         }
         if (sel.empty()) {
@@ -768,6 +796,7 @@ struct Engine {
             J.dest_off = s.dest;
             J.tab_off = x.tab_off[s.d];
             J.tab_cap = x.tab_cap[s.d];
+            J.ge_off = s.ge;
             J.dir = s.d;
             J.n = x.n;
             J.k = x.k;
@@ -822,6 +851,10 @@ struct Engine {
             int64_t c = (int64_t)down[t];
             set_pool.release(s.dest + c, s.nc - c);
             x.lev[s.d].push_back({s.dest, c, c});
+            if (s.d == 1) {  // the new backward level's cardinality table becomes current
+                if (x.ge_off >= 0) meta_pool.release(x.ge_off, card_slots(W));
+                x.ge_off = s.ge;
+            }
             x.dupl[s.d] = 1.0 - (double)c / (double)s.nc;
             x.stored[s.d] += c;
             if (c == 0) finish(x, kFailed, SW_ENOTSYNC);
@@ -848,6 +881,7 @@ struct Engine {
                 M.tile_off = ntiles;
                 M.ntb = (M.b_cnt + mc.tb - 1) / mc.tb;
                 M.slot = t;
+                M.ge_off = x.ge_off;
                 ntiles += ((M.f_cnt + TF - 1) / TF) * M.ntb;
             }
             rc = stage_flush();
@@ -1252,7 +1286,7 @@ size_t sw_workspace_min_bytes(int32_t n_max, int32_t k_max, int32_t count) {
     int W = words_for(n_max);
     int64_t delta = (int64_t)n_max * k_max * count;
     double per_set = (8.0 * W + 8) / 0.55;
-    return small_area_bytes(count, delta) + (size_t)(per_set * ((double)count * (n_max + 1) * 8 + 8192)) + (1 << 20);
+    return small_area_bytes(count, delta, W) + (size_t)(per_set * ((double)count * (n_max + 1) * 8 + 8192)) + (1 << 20);
 }
 
 static int32_t run_instances(std::vector<Inst> &I, const std::vector<uint16_t> *host_delta,

@@ -31,6 +31,7 @@ struct ExpandJob {
     int64_t dest_off;    // arena index where the new level starts
     int64_t tab_off;     // the (instance, direction) hash table
     int64_t tab_cap;
+    int64_t ge_off;      // backward: where the new level's cardinality table goes
     int32_t dir, n, k, pad;  // dir 0 forward (images), 1 backward (preimages)
 };
 
@@ -39,7 +40,14 @@ struct MeetJob {
     int64_t tile_off;    // first tile id of this job
     int64_t ntb;         // tiles along B
     int64_t slot;        // index into best[]
+    int64_t ge_off;      // B's cardinality table (ge[c] = rows with |Y| >= c), or -1
 };
+
+// Backward levels are stored in decreasing order of cardinality (the order of
+// a backward level never affects r, the word or the level sizes).  A level's
+// table ge[c], c = 0 .. 64W + 1, counts its sets with at least c states, so
+// a forward set X can only lie in the first ge[|X|] of them.
+__host__ __device__ constexpr int card_slots(int W) { return 64 * W + 2; }
 
 struct RootJob {
     int64_t f_off, b_off;         // F_0 = {Q} at f_off; B_0 = the n singletons at b_off
@@ -330,12 +338,23 @@ __global__ void __launch_bounds__(256) k_expand(
 
 // A candidate survives when it still owns its slot (it is the first of its
 // set in this level and the set was not seen before).  flag[c] = 1 then;
-// block_cnt[b] = survivors of block b.
-__global__ void __launch_bounds__(kScanThreads) k_flag_count(int64_t ncand, const int64_t *__restrict__ cand_slot,
-                                                             const uint64_t *__restrict__ table,
-                                                             uint8_t *__restrict__ flag, uint32_t *__restrict__ block_cnt) {
+// block_cnt[b] = survivors of block b.  For a backward job the survivors'
+// cardinalities are also counted into hist[job][c] (a block belongs to one
+// job: jobs start on block boundaries).
+template <int W>
+__global__ void __launch_bounds__(kScanThreads) k_flag_count(
+    const ExpandJob *__restrict__ jobs, int njobs, int64_t ncand, const int64_t *__restrict__ cand_slot,
+    const uint64_t *__restrict__ table, const uint64_t *__restrict__ cand_sets, uint8_t *__restrict__ flag,
+    uint32_t *__restrict__ block_cnt, uint32_t *__restrict__ hist) {
     constexpr int IPT = kScanBlock / kScanThreads;
+    constexpr int HN = card_slots(W);
+    __shared__ uint32_t sh[HN];
     int64_t base = (int64_t)blockIdx.x * kScanBlock + threadIdx.x * IPT;
+    const int ji = find_job_expand(jobs, njobs, (int64_t)blockIdx.x * kScanBlock);
+    const bool backward = jobs[ji].dir == 1;
+    if (backward)
+        for (int i = threadIdx.x; i < HN; i += kScanThreads) sh[i] = 0;
+    __syncthreads();
     uint32_t cnt = 0;
 #pragma unroll
     for (int i = 0; i < IPT; ++i) {
@@ -345,6 +364,12 @@ __global__ void __launch_bounds__(kScanThreads) k_flag_count(int64_t ncand, cons
             int64_t s = cand_slot[c];
             f = (s >= 0 && table[s] == kCand + (uint64_t)c) ? 1 : 0;
             flag[c] = f;
+            if (f && backward) {
+                int pc = 0;
+#pragma unroll
+                for (int w = 0; w < W; ++w) pc += __popcll(cand_sets[c * W + w]);
+                atomicAdd(&sh[pc], 1u);
+            }
         }
         cnt += f;
     }
@@ -356,6 +381,26 @@ __global__ void __launch_bounds__(kScanThreads) k_flag_count(int64_t ncand, cons
         uint32_t t = 0;
         for (int i = 0; i < kScanThreads / 32; ++i) t += red[i];
         block_cnt[blockIdx.x] = t;
+    }
+    if (backward)
+        for (int i = threadIdx.x; i < HN; i += kScanThreads)
+            if (sh[i]) atomicAdd(&hist[(int64_t)ji * HN + i], sh[i]);
+}
+
+// Per backward job (one block each): the start of every cardinality bucket
+// in decreasing order of cardinality goes to cursor[job][c], and the level's
+// table ge[c] = sets with at least c states goes to meta[ge_off + c].
+__global__ void k_ge(const ExpandJob *__restrict__ jobs, int hn, const uint32_t *__restrict__ hist,
+                     uint32_t *__restrict__ cursor, int32_t *__restrict__ meta) {
+    const ExpandJob &J = jobs[blockIdx.x];
+    if (J.dir != 1 || threadIdx.x != 0) return;
+    const uint32_t *h = hist + (int64_t)blockIdx.x * hn;
+    uint32_t *cur = cursor + (int64_t)blockIdx.x * hn;
+    uint32_t above = 0;  // sets with more than c states
+    for (int c = hn - 1; c >= 0; --c) {
+        cur[c] = above;
+        above += h[c];
+        meta[J.ge_off + c] = (int32_t)above;
     }
 }
 
@@ -405,15 +450,51 @@ __global__ void __launch_bounds__(kScanThreads) k_compact(
     const ExpandJob *__restrict__ jobs, int njobs, int64_t ncand, const uint8_t *__restrict__ flag,
     const uint64_t *__restrict__ block_off, const uint64_t *__restrict__ cand_sets,
     const int64_t *__restrict__ cand_slot, uint64_t *__restrict__ table, uint64_t *__restrict__ sets,
-    uint64_t *__restrict__ link) {
+    uint64_t *__restrict__ link, uint32_t *__restrict__ cursor) {
     constexpr int IPT = kScanBlock / kScanThreads;
+    constexpr int HN = card_slots(W);
     int64_t base = (int64_t)blockIdx.x * kScanBlock + threadIdx.x * IPT;
+    const int ji = find_job_expand(jobs, njobs, (int64_t)blockIdx.x * kScanBlock);
+    const ExpandJob &J = jobs[ji];
     uint8_t f[IPT];
     uint32_t cnt = 0;
 #pragma unroll
     for (int i = 0; i < IPT; ++i) {
         f[i] = (base + i < ncand) ? flag[base + i] : 0;
         cnt += f[i];
+    }
+    if (J.dir == 1) {
+        // backward: by decreasing cardinality; a block reserves one range per
+        // cardinality (order within a cardinality is free)
+        __shared__ uint32_t sh[HN];
+        __shared__ uint32_t sbase[HN];
+        for (int i = threadIdx.x; i < HN; i += kScanThreads) sh[i] = 0;
+        __syncthreads();
+        int pc[IPT];
+        uint32_t rk[IPT];
+#pragma unroll
+        for (int i = 0; i < IPT; ++i) {
+            pc[i] = 0;
+            rk[i] = 0;
+            if (!f[i]) continue;
+#pragma unroll
+            for (int w = 0; w < W; ++w) pc[i] += __popcll(cand_sets[(base + i) * W + w]);
+            rk[i] = atomicAdd(&sh[pc[i]], 1u);
+        }
+        __syncthreads();
+        for (int i = threadIdx.x; i < HN; i += kScanThreads)
+            sbase[i] = sh[i] ? atomicAdd(&cursor[(int64_t)ji * HN + i], sh[i]) : 0u;
+        __syncthreads();
+#pragma unroll
+        for (int i = 0; i < IPT; ++i) {
+            if (!f[i]) continue;
+            int64_t c = base + i;
+            int64_t g = J.dest_off + (int64_t)(sbase[pc[i]] + rk[i]);
+#pragma unroll
+            for (int w = 0; w < W; ++w) sets[g * W + w] = cand_sets[c * W + w];
+            table[cand_slot[c]] = (uint64_t)g;
+        }
+        return;
     }
     uint32_t x = cnt;  // inclusive warp scan, then across warps
     for (int o = 1; o < 32; o <<= 1) {
@@ -427,7 +508,6 @@ __global__ void __launch_bounds__(kScanThreads) k_compact(
     uint32_t wbefore = 0;
     for (int i = 0; i < (int)(threadIdx.x >> 5); ++i) wbefore += ws[i];
     uint64_t rank = block_off[blockIdx.x] + wbefore + x - cnt;
-    const ExpandJob &J = jobs[find_job_expand(jobs, njobs, base)];
     const uint64_t first = block_off[J.cand_off / kScanBlock];
 #pragma unroll
     for (int i = 0; i < IPT; ++i) {
@@ -436,11 +516,9 @@ __global__ void __launch_bounds__(kScanThreads) k_compact(
         int64_t g = J.dest_off + (int64_t)(rank - first);
 #pragma unroll
         for (int w = 0; w < W; ++w) sets[g * W + w] = cand_sets[c * W + w];
-        if (J.dir == 0) {
-            int64_t local = c - J.cand_off;
-            int64_t p = local / J.k;
-            link[g] = ((uint64_t)(J.parent_off + p) << 8) | (uint64_t)(local - p * J.k);
-        }
+        int64_t local = c - J.cand_off;
+        int64_t p = local / J.k;
+        link[g] = ((uint64_t)(J.parent_off + p) << 8) | (uint64_t)(local - p * J.k);
         table[cand_slot[c]] = (uint64_t)g;
         ++rank;
     }
@@ -627,8 +705,10 @@ __global__ void __launch_bounds__(NT) k_meet_bm(const MeetJob *__restrict__ jobs
                                                 int tf_rows, const uint64_t *__restrict__ sets,
                                                 unsigned long long *best, unsigned long long *pairs_done,
                                                 unsigned long long *and_iters,
-                                                unsigned long long *rows_transposed) {
+                                                unsigned long long *rows_transposed,
+                                                const int32_t *__restrict__ meta) {
     constexpr int LW = bm_lanes_words(W);
+    constexpr int HN = card_slots(W);
     using G = Bm<LW>;
     extern __shared__ __align__(16) uint32_t sT[];  // [64 W][G::kWords]
     __shared__ int64_t s_job;
@@ -679,12 +759,7 @@ __global__ void __launch_bounds__(NT) k_meet_bm(const MeetJob *__restrict__ jobs
         }
         __syncthreads();
         // 2. forward rows, one per warp at a time, in increasing order
-        uint64_t mask[LW];
-#pragma unroll
-        for (int j = 0; j < LW; ++j) {
-            int lim = nb - 64 * (LW * lane + j);
-            mask[j] = lim >= 64 ? ~0ull : (lim > 0 ? ((1ull << lim) - 1) : 0ull);
-        }
+        const int32_t *ge = J.ge_off >= 0 ? meta + J.ge_off : nullptr;
         int64_t f = f0 + warp;
         uint64_t x[W];
         if (f < f1) load_set<W>(sets + (J.f_off + f) * W, x);
@@ -694,6 +769,23 @@ __global__ void __launch_bounds__(NT) k_meet_bm(const MeetJob *__restrict__ jobs
             if (__shfl_sync(0xffffffffu, stop, 0)) break;
             uint64_t xn[W];  // prefetch the warp's next row
             if (f + NW < f1) load_set<W>(sets + (J.f_off + f + NW) * W, xn);
+            // only the backward sets with at least |X| states can contain X
+            int card = 0;
+#pragma unroll
+            for (int w = 0; w < W; ++w) card += __popcll(x[w]);
+            int64_t end = ge ? (int64_t)__ldg(ge + min(card, HN - 1)) : J.b_cnt;
+            int rows = (int)max((int64_t)0, min((int64_t)nb, end - b0));
+            if (rows == 0) {
+#pragma unroll
+                for (int w = 0; w < W; ++w) x[w] = xn[w];
+                continue;
+            }
+            uint64_t mask[LW];
+#pragma unroll
+            for (int j = 0; j < LW; ++j) {
+                int lim = rows - 64 * (LW * lane + j);
+                mask[j] = lim >= 64 ? ~0ull : (lim > 0 ? ((1ull << lim) - 1) : 0ull);
+            }
             uint64_t acc[LW];
 #pragma unroll
             for (int j = 0; j < LW; ++j) acc[j] = mask[j];
@@ -720,7 +812,7 @@ __global__ void __launch_bounds__(NT) k_meet_bm(const MeetJob *__restrict__ jobs
                     alive = __any_sync(0xffffffffu, any != 0);
                 }
             }
-            my_pairs += (unsigned long long)nb;
+            my_pairs += (unsigned long long)rows;
             if (alive) {  // every state of X processed: X lies inside the surviving sets
                 uint64_t any = 0;
 #pragma unroll
