@@ -42,7 +42,7 @@ namespace {
 struct Stats {
     int64_t pairs = 0, candidates = 0;
     int32_t iterations = 0;
-    double meet_ms = 0, expand_ms = 0, compact_ms = 0;
+    double meet_ms = 0, expand_ms = 0, compact_ms = 0, words_ms = 0, run_ms = 0;
     int32_t meet_launches = 0;
     int64_t and_iters = 0;  // bitmap meet: warp-wide AND steps
     int64_t rows_transposed = 0;  // bitmap meet: backward rows transposed into shared memory
@@ -196,6 +196,7 @@ enum InstState { kWaiting = 0, kActive = 1, kDone = 2, kFailed = 3 };
 
 struct Level {
     int64_t off, cnt, cap;  // arena index, sets, slots held in the set pool
+    int64_t ge = -1;        // backward: its cardinality table in the meta pool, or -1
 };
 
 struct Inst {
@@ -203,7 +204,6 @@ struct Inst {
     int64_t delta_off = 0;
     std::vector<Level> lev[2];
     int64_t tab_off[2] = {-1, -1}, tab_cap[2] = {0, 0}, stored[2] = {0, 0};
-    int64_t ge_off = -1;  // cardinality table of the current backward level (-1: B_0)
     double dupl[2] = {0.0, 0.0};
     int32_t state = kWaiting, code = SW_OK, r = -1;
     int32_t evictions = 0;
@@ -226,6 +226,7 @@ struct Layout {
     char *mirror;
     size_t mirror_bytes;
     uint64_t *counts;  // per-job survivors
+    int64_t *ntiles;   // meet tiles of the current iteration
     unsigned long long *best;
     uint32_t *word_status;
     uint32_t *status;
@@ -272,7 +273,8 @@ struct Carver {
 size_t mirror_bytes_for(int32_t count) { return (size_t)std::max(count, 1) * 1024 + (1 << 20); }
 int64_t word_area_for(int32_t count) { return (int64_t)std::max<size_t>((size_t)std::max(count, 1) * 512, 1 << 20); }
 
-int64_t meta_cap_for(int32_t count, int W) { return (int64_t)(2 * std::max(count, 1) + 64) * card_slots(W); }
+// room for the cardinality tables of about 48 backward levels per instance
+int64_t meta_cap_for(int32_t count, int W) { return (int64_t)(48 * std::max(count, 1) + 256) * card_slots(W); }
 
 size_t small_area_bytes(int32_t count, int64_t delta_elems, int W = 9) {
     size_t c = (size_t)std::max(count, 1);
@@ -280,6 +282,7 @@ size_t small_area_bytes(int32_t count, int64_t delta_elems, int W = 9) {
     auto add = [&](size_t x) { b += (x + 255) & ~(size_t)255; };
     add(mirror_bytes_for(count));
     add(c * sizeof(uint64_t));
+    add(sizeof(int64_t));
     add(c * sizeof(unsigned long long));
     add(c * sizeof(uint32_t));
     add(sizeof(uint32_t));
@@ -299,6 +302,7 @@ bool carve(void *ws, size_t bytes, int W, int32_t count, int64_t delta_elems, La
     L.mirror_bytes = mirror_bytes_for(count);
     L.mirror = cv.take<char>(L.mirror_bytes);
     L.counts = cv.take<uint64_t>(c);
+    L.ntiles = cv.take<int64_t>(1);
     L.best = cv.take<unsigned long long>(c);
     L.word_status = cv.take<uint32_t>(c);
     L.status = cv.take<uint32_t>(1);
@@ -401,7 +405,7 @@ MeetCfg meet_cfg(int W) {
 }
 
 template <int W, int R>
-cudaError_t launch_meet_r(const MeetJob *jobs, int njobs, int64_t ntiles, int tb, const uint64_t *sets,
+cudaError_t launch_meet_r(const MeetJob *jobs, int njobs, const int64_t *ntiles, int tb, const uint64_t *sets,
                           unsigned long long *best, unsigned long long *pairs, cudaStream_t st) {
     constexpr int NT = 256;
     auto kern = k_meet<W, R, NT>;
@@ -415,13 +419,12 @@ cudaError_t launch_meet_r(const MeetJob *jobs, int njobs, int64_t ntiles, int tb
     int per_sm = 0;
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, NT, smem);
     int64_t grid = (int64_t)sm_count() * std::max(per_sm, 1);
-    grid = std::min<int64_t>(grid, ntiles);
     kern<<<(unsigned)grid, NT, smem, st>>>(jobs, njobs, ntiles, tb, sets, best, pairs);
     return cudaGetLastError();
 }
 
 template <int W>
-cudaError_t launch_meet_bm(const MeetJob *jobs, int njobs, int64_t ntiles, int tf_rows, const uint64_t *sets,
+cudaError_t launch_meet_bm(const MeetJob *jobs, int njobs, const int64_t *ntiles, int tf_rows, const uint64_t *sets,
                            unsigned long long *best, unsigned long long *pairs, unsigned long long *iters,
                            unsigned long long *rows, const int32_t *meta, cudaStream_t st) {
     constexpr int NT = kBmThreads;
@@ -435,7 +438,7 @@ cudaError_t launch_meet_bm(const MeetJob *jobs, int njobs, int64_t ntiles, int t
     }
     int per_sm = 0;
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, NT, smem);
-    int64_t grid = std::min<int64_t>((int64_t)sm_count() * std::max(per_sm, 1), ntiles);
+    int64_t grid = (int64_t)sm_count() * std::max(per_sm, 1);
     kern<<<(unsigned)grid, NT, smem, st>>>(jobs, njobs, ntiles, tf_rows, sets, best, pairs, iters, rows, meta);
     return cudaGetLastError();
 }
@@ -487,9 +490,11 @@ struct Ops {
         k_job_counts<<<(unsigned)((nj + 255) / 256), 256, 0, st>>>(jobs, nj, nblocks, L.block_off, L.counts);
         return cudaGetLastError();
     }
-    static cudaError_t meet(const MeetJob *jobs, int nj, int64_t ntiles, const MeetCfg &c, const Layout &L,
-                            cudaStream_t st) {
-        g_stats.launches++;
+    static cudaError_t meet(MeetJob *jobs, int nj, const MeetCfg &c, const Layout &L, cudaStream_t st) {
+        g_stats.launches += 2;
+        const int64_t TF = c.algo == 0 ? (int64_t)c.tf_rows : (int64_t)c.nt * c.R;
+        k_meet_prep<<<1, 1024, 0, st>>>(jobs, nj, L.counts, TF, c.tb, L.ntiles);
+        const int64_t *ntiles = L.ntiles;
         if (c.algo == 0)
             return launch_meet_bm<W>(jobs, nj, ntiles, c.tf_rows, L.sets, L.best, L.pairs, L.pairs + 1, L.pairs + 2,
                                      L.meta, st);
@@ -508,7 +513,8 @@ struct Ops {
     static cudaError_t words(const WordJob *jobs, const int64_t *blevels, int nj, uint8_t *base, const Layout &L,
                              cudaStream_t st) {
         g_stats.launches++;
-        k_words<W, 256><<<(unsigned)nj, 256, 0, st>>>(jobs, blevels, L.delta16, L.sets, L.link, base, L.word_status);
+        k_words<W, 256><<<(unsigned)nj, 256, 0, st>>>(jobs, blevels, L.delta16, L.sets, L.link, L.meta, base,
+                                                       L.word_status);
         return cudaGetLastError();
     }
 };
@@ -519,7 +525,7 @@ struct OpTable {
     cudaError_t (*rehash)(const RehashSeg *, int, int64_t, const Layout &, cudaStream_t);
     cudaError_t (*expand)(const ExpandJob *, int, int64_t, const Layout &, cudaStream_t);
     cudaError_t (*compact)(const ExpandJob *, int, int64_t, const Layout &, cudaStream_t);
-    cudaError_t (*meet)(const MeetJob *, int, int64_t, const MeetCfg &, const Layout &, cudaStream_t);
+    cudaError_t (*meet)(MeetJob *, int, const MeetCfg &, const Layout &, cudaStream_t);
     cudaError_t (*words)(const WordJob *, const int64_t *, int, uint8_t *, const Layout &, cudaStream_t);
 };
 
@@ -625,15 +631,16 @@ struct Engine {
 
     void release(Inst &x) {
         for (int d = 0; d < 2; ++d) {
-            for (auto &l : x.lev[d]) set_pool.release(l.off, l.cap);
+            for (auto &l : x.lev[d]) {
+                set_pool.release(l.off, l.cap);
+                if (l.ge >= 0) meta_pool.release(l.ge, card_slots(W));
+            }
             x.lev[d].clear();
             if (x.tab_off[d] >= 0) tab_pool.release(x.tab_off[d], x.tab_cap[d]);
             x.tab_off[d] = -1;
             x.tab_cap[d] = 0;
             x.stored[d] = 0;
         }
-        if (x.ge_off >= 0) meta_pool.release(x.ge_off, card_slots(W));
-        x.ge_off = -1;
     }
 
     void finish(Inst &x, int state, int code) {
@@ -669,8 +676,8 @@ struct Engine {
                 x.lev[d].clear();
                 x.dupl[d] = 0.0;
             }
-            x.lev[0].push_back({f, 1, 1});
-            x.lev[1].push_back({b, x.n, x.n});
+            x.lev[0].push_back({f, 1, 1, -1});
+            x.lev[1].push_back({b, x.n, x.n, -1});
             x.tab_off[0] = t0;
             x.tab_cap[0] = tc0;
             x.tab_off[1] = t1;
@@ -738,14 +745,8 @@ struct Engine {
                 if (nt < 0) continue;
             }
             int64_t dest = set_pool.alloc(nc);
-            int64_t ge = -1;
-            if (dest >= 0 && d == 1) {
-                ge = meta_pool.alloc(card_slots(W));
-                if (ge < 0) {
-                    set_pool.release(dest, nc);
-                    dest = -1;
-                }
-            }
+            // a full table pool only costs the level its cardinality table
+            int64_t ge = (dest >= 0 && d == 1) ? meta_pool.alloc(card_slots(W)) : -1;
             if (dest < 0) {
                 if (nt >= 0) tab_pool.release(nt, ntc);
                 continue;
@@ -820,7 +821,26 @@ struct Engine {
             std::memcpy(f, fills.data(), fills.size() * sizeof(FillJob));
             std::memcpy(g, segs.data(), segs.size() * sizeof(RehashSeg));
         }
+        // meet jobs: the size of the level each job produces is filled in on
+        // the device (k_meet_prep), so the meet follows without a host sync
+        MeetJob *d_mj;
+        MeetJob *mj = stg.take<MeetJob>(nj, &d_mj);
         if (!stg.ok) return SW_EINTERNAL;
+        for (int t = 0; t < nj; ++t) {
+            Sel &s = sel[t];
+            Inst &x = I[s.id];
+            MeetJob &M = mj[t];
+            M.f_off = s.d == 0 ? s.dest : x.lev[0].back().off;
+            M.f_cnt = s.d == 0 ? 0 : x.lev[0].back().cnt;
+            M.b_off = s.d == 1 ? s.dest : x.lev[1].back().off;
+            M.b_cnt = s.d == 1 ? 0 : x.lev[1].back().cnt;
+            M.tile_off = 0;
+            M.ntb = 1;
+            M.slot = t;
+            M.ge_off = s.d == 1 ? s.ge : x.lev[1].back().ge;
+            M.upd = s.d;
+            M.count_idx = t;
+        }
         int rc = stage_flush();
         if (rc) return rc;
         g_stats.candidates += ncand;
@@ -833,79 +853,47 @@ struct Engine {
         if (g_timing) CK(cudaEventRecord(g_ev.ev[1], st));
         CK(ops.compact(d_jobs, nj, ncand, L, st));
         if (g_timing) CK(cudaEventRecord(g_ev.ev[2], st));
-        uint64_t *down = (uint64_t *)g_down.get((nj + 1) * sizeof(uint64_t));
+        CK(cudaMemsetAsync(L.best, 0xFF, nj * sizeof(unsigned long long), st));
+        CK(cudaMemsetAsync(L.pairs, 0, 3 * sizeof(unsigned long long), st));
+        if (g_timing) CK(cudaEventRecord(g_ev.ev[3], st));
+        CK(ops.meet(d_mj, nj, mc, L, st));
+        if (g_timing) CK(cudaEventRecord(g_ev.ev[4], st));
+        g_stats.meet_launches++;
+        // one copy back: counts, status, meet results, counters
+        uint64_t *down = (uint64_t *)g_down.get((2 * nj + 5) * sizeof(uint64_t));
         if (!down) return SW_ECUDA;
+        uint64_t *d_status = down + nj, *d_best = down + nj + 1, *d_pairs = down + 2 * nj + 1;
         CK(cudaMemcpyAsync(down, L.counts, nj * sizeof(uint64_t), cudaMemcpyDeviceToHost, st));
-        CK(cudaMemcpyAsync(down + nj, L.status, sizeof(uint32_t), cudaMemcpyDeviceToHost, st));
+        CK(cudaMemcpyAsync(d_status, L.status, sizeof(uint32_t), cudaMemcpyDeviceToHost, st));
+        CK(cudaMemcpyAsync(d_best, L.best, nj * sizeof(unsigned long long), cudaMemcpyDeviceToHost, st));
+        CK(cudaMemcpyAsync(d_pairs, L.pairs, 3 * sizeof(unsigned long long), cudaMemcpyDeviceToHost, st));
         CK(cudaStreamSynchronize(st));
         if (g_timing) {
             g_stats.expand_ms += elapsed(g_ev.ev[0], g_ev.ev[1]);
             g_stats.compact_ms += elapsed(g_ev.ev[1], g_ev.ev[2]);
+            g_stats.meet_ms += elapsed(g_ev.ev[3], g_ev.ev[4]);
         }
-        if ((uint32_t)(down[nj] & 0xFFFFFFFFu) & kStatusTableFull) return SW_EINTERNAL;
+        if ((uint32_t)(*d_status & 0xFFFFFFFFu) & kStatusTableFull) return SW_EINTERNAL;
+        g_stats.pairs += (int64_t)d_pairs[0];
+        g_stats.and_iters += (int64_t)d_pairs[1];
+        g_stats.rows_transposed += (int64_t)d_pairs[2];
         // new levels; return the unused tail of each destination
-        std::vector<int> advanced;
+        std::vector<int> met;
+        std::vector<unsigned long long> best;
         for (int t = 0; t < nj; ++t) {
             Sel &s = sel[t];
             Inst &x = I[s.id];
             int64_t c = (int64_t)down[t];
             set_pool.release(s.dest + c, s.nc - c);
-            x.lev[s.d].push_back({s.dest, c, c});
-            if (s.d == 1) {  // the new backward level's cardinality table becomes current
-                if (x.ge_off >= 0) meta_pool.release(x.ge_off, card_slots(W));
-                x.ge_off = s.ge;
-            }
+            x.lev[s.d].push_back({s.dest, c, c, s.ge});
             x.dupl[s.d] = 1.0 - (double)c / (double)s.nc;
             x.stored[s.d] += c;
-            if (c == 0) finish(x, kFailed, SW_ENOTSYNC);
-            else advanced.push_back(s.id);
-        }
-        // meet check on the advanced instances
-        std::vector<int> met;
-        std::vector<unsigned long long> best;
-        if (!advanced.empty()) {
-            if (!stage_begin()) return SW_ECUDA;
-            int nm = (int)advanced.size();
-            MeetJob *d_mj;
-            MeetJob *mj = stg.take<MeetJob>(nm, &d_mj);
-            if (!stg.ok) return SW_EINTERNAL;
-            const int64_t TF = mc.algo == 0 ? (int64_t)mc.tf_rows : (int64_t)mc.nt * mc.R;
-            int64_t ntiles = 0;
-            for (int t = 0; t < nm; ++t) {
-                Inst &x = I[advanced[t]];
-                MeetJob &M = mj[t];
-                M.f_off = x.lev[0].back().off;
-                M.f_cnt = x.lev[0].back().cnt;
-                M.b_off = x.lev[1].back().off;
-                M.b_cnt = x.lev[1].back().cnt;
-                M.tile_off = ntiles;
-                M.ntb = (M.b_cnt + mc.tb - 1) / mc.tb;
-                M.slot = t;
-                M.ge_off = x.ge_off;
-                ntiles += ((M.f_cnt + TF - 1) / TF) * M.ntb;
+            if (c == 0) {
+                finish(x, kFailed, SW_ENOTSYNC);
+            } else if (d_best[t] != ~0ull) {
+                met.push_back(s.id);
+                best.push_back(d_best[t]);
             }
-            rc = stage_flush();
-            if (rc) return rc;
-            CK(cudaMemsetAsync(L.best, 0xFF, nm * sizeof(unsigned long long), st));
-            CK(cudaMemsetAsync(L.pairs, 0, 3 * sizeof(unsigned long long), st));
-            if (g_timing) CK(cudaEventRecord(g_ev.ev[3], st));
-            CK(ops.meet(d_mj, nm, ntiles, mc, L, st));
-            if (g_timing) CK(cudaEventRecord(g_ev.ev[4], st));
-            g_stats.meet_launches++;
-            unsigned long long *bd = (unsigned long long *)g_down.get((nm + 3) * sizeof(unsigned long long));
-            if (!bd) return SW_ECUDA;
-            CK(cudaMemcpyAsync(bd, L.best, nm * sizeof(unsigned long long), cudaMemcpyDeviceToHost, st));
-            CK(cudaMemcpyAsync(bd + nm, L.pairs, 3 * sizeof(unsigned long long), cudaMemcpyDeviceToHost, st));
-            CK(cudaStreamSynchronize(st));
-            if (g_timing) g_stats.meet_ms += elapsed(g_ev.ev[3], g_ev.ev[4]);
-            g_stats.pairs += (int64_t)bd[nm];
-            g_stats.and_iters += (int64_t)bd[nm + 1];
-            g_stats.rows_transposed += (int64_t)bd[nm + 2];
-            for (int t = 0; t < nm; ++t)
-                if (bd[t] != ~0ull) {
-                    met.push_back(advanced[t]);
-                    best.push_back(bd[t]);
-                }
         }
         if (!met.empty()) {
             rc = recover_words(met, best);
@@ -937,11 +925,11 @@ struct Engine {
                     finish(x, kFailed, SW_ENOMEM);
                     continue;
                 }
-                size_t need = (wj.size() + 1) * sizeof(WordJob) + (blev.size() + 2 * j) * sizeof(int64_t) + 1024;
+                size_t need = (wj.size() + 1) * sizeof(WordJob) + (blev.size() + 3 * j) * sizeof(int64_t) + 1024;
                 if (!wj.empty() && (!stg.fits(need) || (!device_words && area + r > L.word_area_cap))) break;
                 WordJob J;
                 J.f_arena = x.lev[0].back().off + (int64_t)(best[pos] >> 32);
-                J.blev = (int64_t)(blev.size() / 2);
+                J.blev = (int64_t)(blev.size() / 3);
                 J.word_off = device_words ? x.word_off : area;
                 J.delta_off = x.delta_off;
                 J.i = i;
@@ -953,6 +941,7 @@ struct Engine {
                 for (int m = 0; m < j; ++m) {
                     blev.push_back(x.lev[1][m].off);
                     blev.push_back(x.lev[1][m].cnt);
+                    blev.push_back(x.lev[1][m].ge);
                 }
                 if (!device_words) area += r;
                 wj.push_back(J);
@@ -962,14 +951,16 @@ struct Engine {
             WordJob *d_wj;
             int64_t *d_bl;
             WordJob *hw = stg.take<WordJob>(nw, &d_wj);
-            int64_t *hb = stg.take<int64_t>(std::max<size_t>(blev.size(), 2), &d_bl);
+            int64_t *hb = stg.take<int64_t>(std::max<size_t>(blev.size(), 3), &d_bl);
             if (!stg.ok) return SW_EINTERNAL;
             std::memcpy(hw, wj.data(), nw * sizeof(WordJob));
             if (!blev.empty()) std::memcpy(hb, blev.data(), blev.size() * sizeof(int64_t));
             int rc = stage_flush();
             if (rc) return rc;
             uint8_t *base = device_words ? out_words : L.word_area;
+            if (g_timing) CK(cudaEventRecord(g_ev.ev[5], st));
             CK(ops.words(d_wj, d_bl, nw, base, L, st));
+            if (g_timing) CK(cudaEventRecord(g_ev.ev[6], st));
             uint32_t *ws = (uint32_t *)g_down.get(nw * sizeof(uint32_t));
             if (!ws) return SW_ECUDA;
             CK(cudaMemcpyAsync(ws, L.word_status, nw * sizeof(uint32_t), cudaMemcpyDeviceToHost, st));
@@ -980,6 +971,7 @@ struct Engine {
                 CK(cudaMemcpyAsync(hwd, L.word_area, (size_t)area, cudaMemcpyDeviceToHost, st));
             }
             CK(cudaStreamSynchronize(st));
+            if (g_timing) g_stats.words_ms += elapsed(g_ev.ev[5], g_ev.ev[6]);
             for (int t = 0; t < nw; ++t) {
                 Inst &x = I[wj[t].pad];
                 if (ws[t] != 0) {
@@ -1343,7 +1335,9 @@ static int32_t run_instances(std::vector<Inst> &I, const std::vector<uint16_t> *
     Engine E(W, st, I, L);
     E.device_words = device_words;
     E.out_words = out_words;
+    auto t0 = std::chrono::steady_clock::now();
     int rc = E.run();
+    g_stats.run_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
     if (rc == SW_OK && cudaStreamSynchronize(st) != cudaSuccess) rc = SW_ECUDA;
     return rc;
 }
@@ -1472,7 +1466,7 @@ int32_t sw_batch_device(int32_t count, const int32_t *n, const int32_t *k, const
 int32_t sw_last_stats(int64_t *pairs, int64_t *candidates, int32_t *iterations, double *meet_ms,
                       double *expand_ms, double *compact_ms, int32_t *meet_launches, int64_t *launches,
                       int32_t *waves, int32_t *evictions, int64_t *arena_peak, int64_t *and_iters,
-                      int64_t *rows_transposed) {
+                      int64_t *rows_transposed, double *words_ms, double *run_ms) {
     if (pairs) *pairs = g_stats.pairs;
     if (candidates) *candidates = g_stats.candidates;
     if (iterations) *iterations = g_stats.iterations;
@@ -1486,6 +1480,8 @@ int32_t sw_last_stats(int64_t *pairs, int64_t *candidates, int32_t *iterations, 
     if (arena_peak) *arena_peak = g_stats.arena_peak;
     if (and_iters) *and_iters = g_stats.and_iters;
     if (rows_transposed) *rows_transposed = g_stats.rows_transposed;
+    if (words_ms) *words_ms = g_stats.words_ms;
+    if (run_ms) *run_ms = g_stats.run_ms;
     return SW_OK;
 }
 

@@ -41,7 +41,55 @@ struct MeetJob {
     int64_t ntb;         // tiles along B
     int64_t slot;        // index into best[]
     int64_t ge_off;      // B's cardinality table (ge[c] = rows with |Y| >= c), or -1
+    int32_t upd;         // -1: counts known; 0: f_cnt, 1: b_cnt = counts[count_idx]
+    int32_t count_idx;
 };
+
+// Lays out the meet tiles on the device once the new levels' sizes are
+// known: fills the size of the level each job just produced, its tiles
+// (tf_rows forward rows x tb backward rows; none if a level is empty) and
+// the exclusive scan of tile counts; *ntiles = their total.  One block.
+__global__ void __launch_bounds__(1024) k_meet_prep(MeetJob *__restrict__ jobs, int njobs,
+                                                    const uint64_t *__restrict__ counts, int64_t tf_rows,
+                                                    int64_t tb, int64_t *__restrict__ ntiles) {
+    __shared__ int64_t warp_sum[32];
+    __shared__ int64_t carry;
+    if (threadIdx.x == 0) carry = 0;
+    __syncthreads();
+    for (int base = 0; base < njobs; base += 1024) {
+        int j = base + threadIdx.x;
+        int64_t tiles = 0;
+        if (j < njobs) {
+            MeetJob &M = jobs[j];
+            if (M.upd == 0) M.f_cnt = (int64_t)counts[M.count_idx];
+            if (M.upd == 1) M.b_cnt = (int64_t)counts[M.count_idx];
+            M.ntb = M.b_cnt > 0 ? (M.b_cnt + tb - 1) / tb : 1;
+            tiles = (M.f_cnt > 0 && M.b_cnt > 0) ? ((M.f_cnt + tf_rows - 1) / tf_rows) * M.ntb : 0;
+        }
+        int64_t x = tiles;  // inclusive scan over the block
+        for (int o = 1; o < 32; o <<= 1) {
+            int64_t y = __shfl_up_sync(0xffffffffu, x, o);
+            if ((threadIdx.x & 31) >= o) x += y;
+        }
+        if ((threadIdx.x & 31) == 31) warp_sum[threadIdx.x >> 5] = x;
+        __syncthreads();
+        if (threadIdx.x < 32) {
+            int64_t v = warp_sum[threadIdx.x];
+            for (int o = 1; o < 32; o <<= 1) {
+                int64_t y = __shfl_up_sync(0xffffffffu, v, o);
+                if (threadIdx.x >= o) v += y;
+            }
+            warp_sum[threadIdx.x] = v;
+        }
+        __syncthreads();
+        int64_t before = carry + (threadIdx.x >= 32 ? warp_sum[(threadIdx.x >> 5) - 1] : 0) + x - tiles;
+        if (j < njobs) jobs[j].tile_off = before;
+        __syncthreads();
+        if (threadIdx.x == 1023) carry = before + tiles;
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) *ntiles = carry;
+}
 
 // Backward levels are stored in decreasing order of cardinality (the order of
 // a backward level never affects r, the word or the level sizes).  A level's
@@ -68,7 +116,7 @@ struct RehashSeg {
 
 struct WordJob {
     int64_t f_arena;     // arena index of the meeting forward set X
-    int64_t blev;        // first (offset, count) pair of B_0..B_{j-1} in blevels
+    int64_t blev;        // first (offset, count, table) triple of B_0..B_{j-1} in blevels
     int64_t word_off;    // output position in the word buffer
     int64_t delta_off;
     int32_t i, j, n, k;
@@ -389,7 +437,8 @@ __global__ void __launch_bounds__(kScanThreads) k_flag_count(
 
 // Per backward job (one block each): the start of every cardinality bucket
 // in decreasing order of cardinality goes to cursor[job][c], and the level's
-// table ge[c] = sets with at least c states goes to meta[ge_off + c].
+// table ge[c] = sets with at least c states goes to meta[ge_off + c] (when
+// the job has a table; ge_off = -1 when the table pool was full).
 __global__ void k_ge(const ExpandJob *__restrict__ jobs, int hn, const uint32_t *__restrict__ hist,
                      uint32_t *__restrict__ cursor, int32_t *__restrict__ meta) {
     const ExpandJob &J = jobs[blockIdx.x];
@@ -400,7 +449,7 @@ __global__ void k_ge(const ExpandJob *__restrict__ jobs, int hn, const uint32_t 
     for (int c = hn - 1; c >= 0; --c) {
         cur[c] = above;
         above += h[c];
-        meta[J.ge_off + c] = (int32_t)above;
+        if (J.ge_off >= 0) meta[J.ge_off + c] = (int32_t)above;
     }
 }
 
@@ -551,9 +600,11 @@ __global__ void k_job_counts(const ExpandJob *__restrict__ jobs, int njobs, int6
 // rare hit is located by a second pass.  A tile whose first row is beyond
 // the best f already found is skipped.
 template <int W, int R, int NT>
-__global__ void __launch_bounds__(NT) k_meet(const MeetJob *__restrict__ jobs, int njobs, int64_t ntiles,
-                                             int tb, const uint64_t *__restrict__ sets,
-                                             unsigned long long *best, unsigned long long *pairs_done) {
+__global__ void __launch_bounds__(NT) k_meet(const MeetJob *__restrict__ jobs, int njobs,
+                                             const int64_t *__restrict__ ntiles_p, int tb,
+                                             const uint64_t *__restrict__ sets, unsigned long long *best,
+                                             unsigned long long *pairs_done) {
+    const int64_t ntiles = *ntiles_p;
     extern __shared__ __align__(16) uint64_t sB[];  // [W][tb]
     __shared__ int64_t s_job;
     __shared__ int s_skip;
@@ -701,8 +752,9 @@ __device__ __forceinline__ uint32_t warp_transpose32(uint32_t v, int lane) {
 }
 
 template <int W, int NT>
-__global__ void __launch_bounds__(NT) k_meet_bm(const MeetJob *__restrict__ jobs, int njobs, int64_t ntiles,
-                                                int tf_rows, const uint64_t *__restrict__ sets,
+__global__ void __launch_bounds__(NT) k_meet_bm(const MeetJob *__restrict__ jobs, int njobs,
+                                                const int64_t *__restrict__ ntiles_p, int tf_rows,
+                                                const uint64_t *__restrict__ sets,
                                                 unsigned long long *best, unsigned long long *pairs_done,
                                                 unsigned long long *and_iters,
                                                 unsigned long long *rows_transposed,
@@ -710,6 +762,7 @@ __global__ void __launch_bounds__(NT) k_meet_bm(const MeetJob *__restrict__ jobs
     constexpr int LW = bm_lanes_words(W);
     constexpr int HN = card_slots(W);
     using G = Bm<LW>;
+    const int64_t ntiles = *ntiles_p;
     extern __shared__ __align__(16) uint32_t sT[];  // [64 W][G::kWords]
     __shared__ int64_t s_job;
     __shared__ int s_skip;
@@ -854,17 +907,20 @@ __global__ void __launch_bounds__(NT) k_meet_bm(const MeetJob *__restrict__ jobs
 // set that m more letters can map to one state, and by minimality of r that
 // backward set was first reached at depth m).  Finally |delta(Q, xy)| = 1 is
 // checked.  word_status[slot]: 0 ok, else kStatusWordFail/kStatusVerifyFail.
+// blevels holds (offset, count, cardinality table or -1) per backward level.
 template <int W, int NT>
 __global__ void __launch_bounds__(NT) k_words(const WordJob *__restrict__ jobs,
                                               const int64_t *__restrict__ blevels,
                                               const uint16_t *__restrict__ delta16,
                                               const uint64_t *__restrict__ sets,
-                                              const uint64_t *__restrict__ link, uint8_t *__restrict__ words,
-                                              uint32_t *__restrict__ word_status) {
+                                              const uint64_t *__restrict__ link, const int32_t *__restrict__ meta,
+                                              uint8_t *__restrict__ words, uint32_t *__restrict__ word_status) {
+    constexpr int HN = card_slots(W);
     const WordJob J = jobs[blockIdx.x];
     uint8_t *out = words + J.word_off;
     __shared__ int s_choice;
     __shared__ uint32_t s_fail;
+    __shared__ volatile int s_found;
     if (threadIdx.x == 0) {
         s_fail = 0;
         uint64_t g = (uint64_t)J.f_arena;
@@ -879,19 +935,31 @@ __global__ void __launch_bounds__(NT) k_words(const WordJob *__restrict__ jobs,
     __syncthreads();
     for (int t = 0; t < J.j; ++t) {
         int m = J.j - 1 - t;
-        int64_t off = blevels[2 * (J.blev + m)], cnt = blevels[2 * (J.blev + m) + 1];
+        const int64_t *lv = blevels + 3 * (J.blev + m);
+        int64_t off = lv[0], cnt = lv[1], ge = lv[2];
         if (threadIdx.x == 0) s_choice = -1;
         __syncthreads();
         for (int a = 0; a < J.k; ++a) {
             uint64_t T[W];
             image<W>(S, delta16 + J.delta_off + (int64_t)a * J.n, T);
+            // the level is in decreasing cardinality: only its first ge[|T|]
+            // sets can contain T
+            int card = 0;
+#pragma unroll
+            for (int w = 0; w < W; ++w) card += __popcll(T[w]);
+            int64_t lim = ge >= 0 ? (int64_t)meta[ge + min(card, HN - 1)] : cnt;
+            if (threadIdx.x == 0) s_found = 0;
+            __syncthreads();
             int found = 0;
-            for (int64_t b = threadIdx.x; b < cnt; b += NT) {
+            for (int64_t b = threadIdx.x; b < lim && !s_found; b += NT) {
                 const uint64_t *y = sets + (off + b) * W;
                 uint64_t acc = 0;
 #pragma unroll
                 for (int w = 0; w < W; ++w) acc |= T[w] & ~y[w];
-                if (acc == 0) { found = 1; break; }
+                if (acc == 0) {
+                    found = 1;
+                    s_found = 1;
+                }
             }
             if (__syncthreads_or(found)) {
                 if (threadIdx.x == 0) s_choice = a;
