@@ -240,6 +240,7 @@ struct Layout {
     int64_t cap_meta;
     // pools
     uint64_t *sets, *link;
+    uint32_t *perm;  // forward levels: canonical position of the i-th set by cardinality
     int64_t cap_sets;
     uint64_t *table;
     int64_t cap_table;
@@ -320,7 +321,7 @@ bool carve(void *ws, size_t bytes, int W, int32_t count, int64_t delta_elems, La
     if (rest < 256 * 1024) return false;
     rest -= 16 * 1024;
     // bytes: sets 55%, table 25%, candidates 20%
-    double set_b = 8.0 * W + 8, cand_b = 8.0 * W + 8 + 1 + 12.0 / kScanBlock;
+    double set_b = 8.0 * W + 12, cand_b = 8.0 * W + 8 + 1 + 12.0 / kScanBlock;
     int64_t S = (int64_t)(0.55 * rest / set_b);
     int64_t T = (int64_t)(0.25 * rest / 8.0);
     int64_t C = (int64_t)(0.20 * rest / cand_b);
@@ -329,6 +330,7 @@ bool carve(void *ws, size_t bytes, int W, int32_t count, int64_t delta_elems, La
     int64_t nblocks = C / kScanBlock;
     L.sets = cv.take<uint64_t>((size_t)S * W);
     L.link = cv.take<uint64_t>((size_t)S);
+    L.perm = cv.take<uint32_t>((size_t)S);
     L.table = cv.take<uint64_t>((size_t)T);
     L.cand_sets = cv.take<uint64_t>((size_t)C * W);
     L.cand_slot = cv.take<int64_t>((size_t)C);
@@ -425,7 +427,7 @@ cudaError_t launch_meet_r(const MeetJob *jobs, int njobs, const int64_t *ntiles,
 
 template <int W>
 cudaError_t launch_meet_bm(const MeetJob *jobs, int njobs, const int64_t *ntiles, int tf_rows, const uint64_t *sets,
-                           unsigned long long *best, unsigned long long *pairs, unsigned long long *iters,
+                           const uint32_t *perm, unsigned long long *best, unsigned long long *pairs, unsigned long long *iters,
                            unsigned long long *rows, const int32_t *meta, cudaStream_t st) {
     constexpr int NT = kBmThreads;
     auto kern = k_meet_bm<W, NT>;
@@ -439,7 +441,7 @@ cudaError_t launch_meet_bm(const MeetJob *jobs, int njobs, const int64_t *ntiles
     int per_sm = 0;
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, NT, smem);
     int64_t grid = (int64_t)sm_count() * std::max(per_sm, 1);
-    kern<<<(unsigned)grid, NT, smem, st>>>(jobs, njobs, ntiles, tf_rows, sets, best, pairs, iters, rows, meta);
+    kern<<<(unsigned)grid, NT, smem, st>>>(jobs, njobs, ntiles, tf_rows, sets, perm, best, pairs, iters, rows, meta);
     return cudaGetLastError();
 }
 
@@ -457,7 +459,7 @@ struct Ops {
         for (int b = 0; b < nj; b += 65535) {
             dim3 grid((unsigned)((nmax + 1 + 255) / 256), (unsigned)std::min(65535, nj - b));
             g_stats.launches++;
-            k_roots<W><<<grid, 256, 0, st>>>(j + b, L.sets, L.link, L.table, L.status);
+            k_roots<W><<<grid, 256, 0, st>>>(j + b, L.sets, L.link, L.perm, L.table, L.status);
         }
         return cudaGetLastError();
     }
@@ -486,7 +488,8 @@ struct Ops {
         k_scan_blocks<<<1, 1024, 0, st>>>(nblocks, L.block_cnt, L.block_off);
         k_ge<<<(unsigned)nj, 32, 0, st>>>(jobs, HN, L.hist, L.cursor, L.meta);
         k_compact<W><<<(unsigned)nblocks, kScanThreads, 0, st>>>(jobs, nj, ncand, L.flag, L.block_off, L.cand_sets,
-                                                                 L.cand_slot, L.table, L.sets, L.link, L.cursor);
+                                                                 L.cand_slot, L.table, L.sets, L.link, L.perm,
+                                                                 L.cursor);
         k_job_counts<<<(unsigned)((nj + 255) / 256), 256, 0, st>>>(jobs, nj, nblocks, L.block_off, L.counts);
         return cudaGetLastError();
     }
@@ -496,8 +499,8 @@ struct Ops {
         k_meet_prep<<<1, 1024, 0, st>>>(jobs, nj, L.counts, TF, c.tb, L.ntiles);
         const int64_t *ntiles = L.ntiles;
         if (c.algo == 0)
-            return launch_meet_bm<W>(jobs, nj, ntiles, c.tf_rows, L.sets, L.best, L.pairs, L.pairs + 1, L.pairs + 2,
-                                     L.meta, st);
+            return launch_meet_bm<W>(jobs, nj, ntiles, c.tf_rows, L.sets, L.perm, L.best, L.pairs, L.pairs + 1,
+                                     L.pairs + 2, L.meta, st);
         switch (c.R) {
             case 1:
                 if constexpr (W >= 3) return launch_meet_r<W, 1>(jobs, nj, ntiles, c.tb, L.sets, L.best, L.pairs, st);

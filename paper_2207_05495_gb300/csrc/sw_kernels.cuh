@@ -256,7 +256,8 @@ __device__ __forceinline__ void insert_stored(uint64_t *table, int64_t tab_off, 
 // set; blockIdx.y = instance.
 template <int W>
 __global__ void k_roots(const RootJob *__restrict__ jobs, uint64_t *__restrict__ sets,
-                        uint64_t *__restrict__ link, uint64_t *table, uint32_t *status) {
+                        uint64_t *__restrict__ link, uint32_t *__restrict__ perm, uint64_t *table,
+                        uint32_t *status) {
     const RootJob J = jobs[blockIdx.y];
     for (int t = blockIdx.x * blockDim.x + threadIdx.x; t <= J.n; t += gridDim.x * blockDim.x) {
         uint64_t s[W];
@@ -271,6 +272,7 @@ __global__ void k_roots(const RootJob *__restrict__ jobs, uint64_t *__restrict__
             g = J.f_off;
             dir = 0;
             link[g] = ~0ull;
+            perm[g] = 0;
         } else {
             int q = t - 1;
 #pragma unroll
@@ -386,9 +388,9 @@ __global__ void __launch_bounds__(256) k_expand(
 
 // A candidate survives when it still owns its slot (it is the first of its
 // set in this level and the set was not seen before).  flag[c] = 1 then;
-// block_cnt[b] = survivors of block b.  For a backward job the survivors'
-// cardinalities are also counted into hist[job][c] (a block belongs to one
-// job: jobs start on block boundaries).
+// block_cnt[b] = survivors of block b.  The survivors' cardinalities are
+// also counted into hist[job][c] (a block belongs to one job: jobs start on
+// block boundaries).
 template <int W>
 __global__ void __launch_bounds__(kScanThreads) k_flag_count(
     const ExpandJob *__restrict__ jobs, int njobs, int64_t ncand, const int64_t *__restrict__ cand_slot,
@@ -399,9 +401,7 @@ __global__ void __launch_bounds__(kScanThreads) k_flag_count(
     __shared__ uint32_t sh[HN];
     int64_t base = (int64_t)blockIdx.x * kScanBlock + threadIdx.x * IPT;
     const int ji = find_job_expand(jobs, njobs, (int64_t)blockIdx.x * kScanBlock);
-    const bool backward = jobs[ji].dir == 1;
-    if (backward)
-        for (int i = threadIdx.x; i < HN; i += kScanThreads) sh[i] = 0;
+    for (int i = threadIdx.x; i < HN; i += kScanThreads) sh[i] = 0;
     __syncthreads();
     uint32_t cnt = 0;
 #pragma unroll
@@ -412,7 +412,7 @@ __global__ void __launch_bounds__(kScanThreads) k_flag_count(
             int64_t s = cand_slot[c];
             f = (s >= 0 && table[s] == kCand + (uint64_t)c) ? 1 : 0;
             flag[c] = f;
-            if (f && backward) {
+            if (f) {
                 int pc = 0;
 #pragma unroll
                 for (int w = 0; w < W; ++w) pc += __popcll(cand_sets[c * W + w]);
@@ -430,21 +430,29 @@ __global__ void __launch_bounds__(kScanThreads) k_flag_count(
         for (int i = 0; i < kScanThreads / 32; ++i) t += red[i];
         block_cnt[blockIdx.x] = t;
     }
-    if (backward)
-        for (int i = threadIdx.x; i < HN; i += kScanThreads)
-            if (sh[i]) atomicAdd(&hist[(int64_t)ji * HN + i], sh[i]);
+    for (int i = threadIdx.x; i < HN; i += kScanThreads)
+        if (sh[i]) atomicAdd(&hist[(int64_t)ji * HN + i], sh[i]);
 }
 
-// Per backward job (one block each): the start of every cardinality bucket
-// in decreasing order of cardinality goes to cursor[job][c], and the level's
-// table ge[c] = sets with at least c states goes to meta[ge_off + c] (when
-// the job has a table; ge_off = -1 when the table pool was full).
+// Per job (one block each): the start of every cardinality bucket goes to
+// cursor[job][c] - in decreasing order of cardinality for a backward job,
+// whose table ge[c] = sets with at least c states also goes to
+// meta[ge_off + c] (when the job has a table; ge_off = -1 when the table
+// pool was full); in increasing order for a forward job (its permutation).
 __global__ void k_ge(const ExpandJob *__restrict__ jobs, int hn, const uint32_t *__restrict__ hist,
                      uint32_t *__restrict__ cursor, int32_t *__restrict__ meta) {
     const ExpandJob &J = jobs[blockIdx.x];
-    if (J.dir != 1 || threadIdx.x != 0) return;
+    if (threadIdx.x != 0) return;
     const uint32_t *h = hist + (int64_t)blockIdx.x * hn;
     uint32_t *cur = cursor + (int64_t)blockIdx.x * hn;
+    if (J.dir == 0) {
+        uint32_t below = 0;  // sets with fewer than c states
+        for (int c = 0; c < hn; ++c) {
+            cur[c] = below;
+            below += h[c];
+        }
+        return;
+    }
     uint32_t above = 0;  // sets with more than c states
     for (int c = hn - 1; c >= 0; --c) {
         cur[c] = above;
@@ -499,7 +507,7 @@ __global__ void __launch_bounds__(kScanThreads) k_compact(
     const ExpandJob *__restrict__ jobs, int njobs, int64_t ncand, const uint8_t *__restrict__ flag,
     const uint64_t *__restrict__ block_off, const uint64_t *__restrict__ cand_sets,
     const int64_t *__restrict__ cand_slot, uint64_t *__restrict__ table, uint64_t *__restrict__ sets,
-    uint64_t *__restrict__ link, uint32_t *__restrict__ cursor) {
+    uint64_t *__restrict__ link, uint32_t *__restrict__ perm, uint32_t *__restrict__ cursor) {
     constexpr int IPT = kScanBlock / kScanThreads;
     constexpr int HN = card_slots(W);
     int64_t base = (int64_t)blockIdx.x * kScanBlock + threadIdx.x * IPT;
@@ -512,28 +520,29 @@ __global__ void __launch_bounds__(kScanThreads) k_compact(
         f[i] = (base + i < ncand) ? flag[base + i] : 0;
         cnt += f[i];
     }
+    // every survivor's place in its cardinality bucket: a block reserves one
+    // range per cardinality (the order inside a cardinality is free)
+    __shared__ uint32_t sh[HN];
+    __shared__ uint32_t sbase[HN];
+    for (int i = threadIdx.x; i < HN; i += kScanThreads) sh[i] = 0;
+    __syncthreads();
+    int pc[IPT];
+    uint32_t rk[IPT];
+#pragma unroll
+    for (int i = 0; i < IPT; ++i) {
+        pc[i] = 0;
+        rk[i] = 0;
+        if (!f[i]) continue;
+#pragma unroll
+        for (int w = 0; w < W; ++w) pc[i] += __popcll(cand_sets[(base + i) * W + w]);
+        rk[i] = atomicAdd(&sh[pc[i]], 1u);
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < HN; i += kScanThreads)
+        sbase[i] = sh[i] ? atomicAdd(&cursor[(int64_t)ji * HN + i], sh[i]) : 0u;
+    __syncthreads();
     if (J.dir == 1) {
-        // backward: by decreasing cardinality; a block reserves one range per
-        // cardinality (order within a cardinality is free)
-        __shared__ uint32_t sh[HN];
-        __shared__ uint32_t sbase[HN];
-        for (int i = threadIdx.x; i < HN; i += kScanThreads) sh[i] = 0;
-        __syncthreads();
-        int pc[IPT];
-        uint32_t rk[IPT];
-#pragma unroll
-        for (int i = 0; i < IPT; ++i) {
-            pc[i] = 0;
-            rk[i] = 0;
-            if (!f[i]) continue;
-#pragma unroll
-            for (int w = 0; w < W; ++w) pc[i] += __popcll(cand_sets[(base + i) * W + w]);
-            rk[i] = atomicAdd(&sh[pc[i]], 1u);
-        }
-        __syncthreads();
-        for (int i = threadIdx.x; i < HN; i += kScanThreads)
-            sbase[i] = sh[i] ? atomicAdd(&cursor[(int64_t)ji * HN + i], sh[i]) : 0u;
-        __syncthreads();
+        // backward: the level itself in decreasing cardinality
 #pragma unroll
         for (int i = 0; i < IPT; ++i) {
             if (!f[i]) continue;
@@ -545,6 +554,9 @@ __global__ void __launch_bounds__(kScanThreads) k_compact(
         }
         return;
     }
+    // forward: the level in canonical (parent, letter) order, plus its
+    // permutation perm[dest + i] = canonical position of the i-th set in
+    // increasing cardinality
     uint32_t x = cnt;  // inclusive warp scan, then across warps
     for (int o = 1; o < 32; o <<= 1) {
         uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
@@ -568,6 +580,7 @@ __global__ void __launch_bounds__(kScanThreads) k_compact(
         int64_t local = c - J.cand_off;
         int64_t p = local / J.k;
         link[g] = ((uint64_t)(J.parent_off + p) << 8) | (uint64_t)(local - p * J.k);
+        perm[J.dest_off + sbase[pc[i]] + rk[i]] = (uint32_t)(rank - first);
         table[cand_slot[c]] = (uint64_t)g;
         ++rank;
     }
@@ -714,9 +727,13 @@ __global__ void __launch_bounds__(NT) k_meet(const MeetJob *__restrict__ jobs, i
 // warp takes one forward set X at a time; lane l holds 64*LW bits of the
 // running AND and the warp stops as soon as every lane is zero (after about
 // five states of X on random instances, against 2W LOP3 per pair for the
-// direct test).  Rows of F are taken in increasing order, so the first
-// survivor of a warp is its least meeting f; a tile whose first row lies
-// beyond the best f found so far is skipped.
+// direct test).  Forward rows are visited in increasing cardinality (the
+// level's permutation) and backward sets sit in decreasing cardinality, so
+// X needs only the first ge[|X|] backward sets: a row stops at that bound,
+// a warp stops at its first row with no candidate in the chunk, and a tile
+// whose first (smallest) row has none is skipped before it is transposed.
+// The least meeting canonical position f is kept with atomicMin; rows at or
+// past the best f found so far are passed over.
 //
 // Shared layout: M_q occupies kBmWords(LW) 32-bit words; lane l's 2*LW
 // words (rows 64*LW*l ..) sit at unit (l ^ (q & 31)) of the row, so that
@@ -755,6 +772,7 @@ template <int W, int NT>
 __global__ void __launch_bounds__(NT) k_meet_bm(const MeetJob *__restrict__ jobs, int njobs,
                                                 const int64_t *__restrict__ ntiles_p, int tf_rows,
                                                 const uint64_t *__restrict__ sets,
+                                                const uint32_t *__restrict__ perm,
                                                 unsigned long long *best, unsigned long long *pairs_done,
                                                 unsigned long long *and_iters,
                                                 unsigned long long *rows_transposed,
@@ -779,10 +797,22 @@ __global__ void __launch_bounds__(NT) k_meet_bm(const MeetJob *__restrict__ jobs
             }
             s_job = lo;
             const MeetJob &J = jobs[lo];
-            int64_t tf = (tile - J.tile_off) / J.ntb;
-            unsigned long long cur = *(volatile unsigned long long *)(best + J.slot);
-            s_best = cur;
-            s_skip = ((int64_t)(cur >> 32) < tf * tf_rows) ? 1 : 0;
+            const int64_t local = tile - J.tile_off;
+            const int64_t tf = local / J.ntb;
+            const int64_t b0 = (local - tf * J.ntb) * G::kRows;
+            // forward rows come in increasing cardinality: the tile's first
+            // row has the fewest states, and no backward set of this chunk
+            // can hold it when the chunk starts past ge[that cardinality]
+            int skip = 0;
+            if (J.ge_off >= 0) {
+                const uint32_t f_first = perm[J.f_off + tf * tf_rows];
+                int card = 0;
+#pragma unroll
+                for (int w = 0; w < W; ++w) card += __popcll(sets[(J.f_off + f_first) * W + w]);
+                skip = b0 >= (int64_t)meta[J.ge_off + min(card, HN - 1)];
+            }
+            s_best = *(volatile unsigned long long *)(best + J.slot);
+            s_skip = skip;
         }
         __syncthreads();
         if (s_skip) { __syncthreads(); continue; }
@@ -791,8 +821,8 @@ __global__ void __launch_bounds__(NT) k_meet_bm(const MeetJob *__restrict__ jobs
         const int64_t tf = local / J.ntb;
         const int64_t b0 = (local - tf * J.ntb) * G::kRows;
         const int nb = (int)min((int64_t)G::kRows, J.b_cnt - b0);
-        const int64_t f0 = tf * tf_rows;
-        const int64_t f1 = min(f0 + tf_rows, J.f_cnt);
+        const int64_t i0 = tf * tf_rows;
+        const int64_t i1 = min(i0 + tf_rows, J.f_cnt);
         // 1. transpose the backward chunk: group g = rows 32g..32g+31
         my_rows += (unsigned long long)nb;
         for (int g = warp; g < G::kRows / 32; g += NW) {
@@ -811,79 +841,87 @@ __global__ void __launch_bounds__(NT) k_meet_bm(const MeetJob *__restrict__ jobs
             }
         }
         __syncthreads();
-        // 2. forward rows, one per warp at a time, in increasing order
+        // 2. forward rows (in increasing cardinality), one per warp at a time;
+        //    f is the row's canonical position, and only the least meeting f
+        //    matters, so rows at or past the best f found are passed over
         const int32_t *ge = J.ge_off >= 0 ? meta + J.ge_off : nullptr;
-        int64_t f = f0 + warp;
+        int64_t i = i0 + warp;
+        uint32_t f = 0;
         uint64_t x[W];
-        if (f < f1) load_set<W>(sets + (J.f_off + f) * W, x);
-        for (; f < f1; f += NW) {
+        if (i < i1) {
+            f = __ldg(perm + J.f_off + i);
+            load_set<W>(sets + (J.f_off + f) * W, x);
+        }
+        for (; i < i1; i += NW) {
+            uint32_t fn = 0;  // prefetch the warp's next row
+            uint64_t xn[W];
+            if (i + NW < i1) {
+                fn = __ldg(perm + J.f_off + i + NW);
+                load_set<W>(sets + (J.f_off + fn) * W, xn);
+            }
             // lane 0 reads the shared best; the whole warp follows its decision
-            int stop = (int64_t)(*(volatile unsigned long long *)&s_best >> 32) < f;
-            if (__shfl_sync(0xffffffffu, stop, 0)) break;
-            uint64_t xn[W];  // prefetch the warp's next row
-            if (f + NW < f1) load_set<W>(sets + (J.f_off + f + NW) * W, xn);
+            int pass = (int64_t)(*(volatile unsigned long long *)&s_best >> 32) <= (int64_t)f;
             // only the backward sets with at least |X| states can contain X
             int card = 0;
 #pragma unroll
             for (int w = 0; w < W; ++w) card += __popcll(x[w]);
             int64_t end = ge ? (int64_t)__ldg(ge + min(card, HN - 1)) : J.b_cnt;
             int rows = (int)max((int64_t)0, min((int64_t)nb, end - b0));
-            if (rows == 0) {
+            if (end <= b0) {  // later rows have at least as many states: none fits here
 #pragma unroll
                 for (int w = 0; w < W; ++w) x[w] = xn[w];
-                continue;
+                break;
             }
-            uint64_t mask[LW];
+            if (!__shfl_sync(0xffffffffu, pass, 0)) {
+                uint64_t acc[LW];
 #pragma unroll
-            for (int j = 0; j < LW; ++j) {
-                int lim = rows - 64 * (LW * lane + j);
-                mask[j] = lim >= 64 ? ~0ull : (lim > 0 ? ((1ull << lim) - 1) : 0ull);
-            }
-            uint64_t acc[LW];
+                for (int j = 0; j < LW; ++j) {
+                    int lim = rows - 64 * (LW * lane + j);
+                    acc[j] = lim >= 64 ? ~0ull : (lim > 0 ? ((1ull << lim) - 1) : 0ull);
+                }
+                bool alive = true;
 #pragma unroll
-            for (int j = 0; j < LW; ++j) acc[j] = mask[j];
-            bool alive = true;
-#pragma unroll
-            for (int h = 0; h < 2 * W; ++h) {
-                uint32_t bits = (h & 1) ? (uint32_t)(x[h >> 1] >> 32) : (uint32_t)x[h >> 1];
-                while (bits && alive) {
-                    const int q = 32 * h + __ffs(bits) - 1;
-                    bits &= bits - 1;
-                    const uint32_t *p = sT + q * G::kWords + ((lane ^ (q & 31)) * G::kUnit);
-                    uint64_t any;
-                    if constexpr (LW == 2) {
-                        uint4 v = *reinterpret_cast<const uint4 *>(p);
-                        acc[0] &= ((uint64_t)v.y << 32) | v.x;
-                        acc[LW - 1] &= ((uint64_t)v.w << 32) | v.z;
-                        any = acc[0] | acc[LW - 1];
-                    } else {
-                        uint2 v = *reinterpret_cast<const uint2 *>(p);
-                        acc[0] &= ((uint64_t)v.y << 32) | v.x;
-                        any = acc[0];
+                for (int h = 0; h < 2 * W; ++h) {
+                    uint32_t bits = (h & 1) ? (uint32_t)(x[h >> 1] >> 32) : (uint32_t)x[h >> 1];
+                    while (bits && alive) {
+                        const int q = 32 * h + __ffs(bits) - 1;
+                        bits &= bits - 1;
+                        const uint32_t *p = sT + q * G::kWords + ((lane ^ (q & 31)) * G::kUnit);
+                        uint64_t any;
+                        if constexpr (LW == 2) {
+                            uint4 v = *reinterpret_cast<const uint4 *>(p);
+                            acc[0] &= ((uint64_t)v.y << 32) | v.x;
+                            acc[LW - 1] &= ((uint64_t)v.w << 32) | v.z;
+                            any = acc[0] | acc[LW - 1];
+                        } else {
+                            uint2 v = *reinterpret_cast<const uint2 *>(p);
+                            acc[0] &= ((uint64_t)v.y << 32) | v.x;
+                            any = acc[0];
+                        }
+                        ++my_iters;
+                        alive = __any_sync(0xffffffffu, any != 0);
                     }
-                    ++my_iters;
-                    alive = __any_sync(0xffffffffu, any != 0);
+                }
+                my_pairs += (unsigned long long)rows;
+                if (alive) {  // every state of X processed: X lies inside the surviving sets
+                    uint64_t any = 0;
+#pragma unroll
+                    for (int j = 0; j < LW; ++j) any |= acc[j];
+                    unsigned ball = __ballot_sync(0xffffffffu, any != 0);
+                    if (lane == __ffs(ball) - 1) {
+                        int j = 0;
+#pragma unroll
+                        for (int t = LW - 1; t >= 0; --t)
+                            if (acc[t]) j = t;
+                        unsigned long long key =
+                            ((unsigned long long)f << 32) |
+                            (unsigned long long)(b0 + 64 * (LW * lane + j) + __ffsll((long long)acc[j]) - 1);
+                        atomicMin(&s_best, key);
+                        atomicMin(best + J.slot, key);
+                    }
                 }
             }
-            my_pairs += (unsigned long long)rows;
-            if (alive) {  // every state of X processed: X lies inside the surviving sets
-                uint64_t any = 0;
-#pragma unroll
-                for (int j = 0; j < LW; ++j) any |= acc[j];
-                unsigned ball = __ballot_sync(0xffffffffu, any != 0);
-                if (lane == __ffs(ball) - 1) {
-                    int j = 0;
-#pragma unroll
-                    for (int t = LW - 1; t >= 0; --t)
-                        if (acc[t]) j = t;
-                    unsigned long long key =
-                        ((unsigned long long)f << 32) |
-                        (unsigned long long)(b0 + 64 * (LW * lane + j) + __ffsll((long long)acc[j]) - 1);
-                    atomicMin(&s_best, key);
-                    atomicMin(best + J.slot, key);
-                }
-                break;  // later rows of this warp cannot give a smaller f
-            }
+            f = fn;
 #pragma unroll
             for (int w = 0; w < W; ++w) x[w] = xn[w];
         }
