@@ -442,7 +442,8 @@ def main():
         "kernel_ms_per_step": {"meet": meet_ms, "expand": sum(s["expand_ms"] for s in stats) / len(stats),
                                "compact": sum(s["compact_ms"] for s in stats) / len(stats),
                                "words": sum(s["words_ms"] for s in stats) / len(stats),
-                               "host_wall": sum(s["run_ms"] for s in stats) / len(stats)},
+                               "host_wall": sum(s["run_ms"] for s in stats) / len(stats),
+                               "host_wait": sum(s["sync_ms"] for s in stats) / len(stats)},
         "iterations_per_step": st["iterations"], "waves": st["waves"], "evictions": st["evictions"],
         "arena_peak_sets": st["arena_peak"],
         "one_at_a_time": {"value": m / one_s, "unit": "instances/s", "sample": f"first {m} instances",

@@ -201,12 +201,15 @@ int32_t sw_batch_device(int32_t count, const int32_t *n, const int32_t *k,
  *                 bitmap meet kernel (once per tile).
  *   words_ms:     device time of the word-recovery kernel (with timing on).
  *   run_ms:       host wall time of the whole search.
+ *   sync_ms:      part of run_ms spent waiting for the stream; the rest is
+ *                 host work between launches.
  */
 int32_t sw_last_stats(int64_t *pairs, int64_t *candidates, int32_t *iterations,
                       double *meet_ms, double *expand_ms, double *compact_ms,
                       int32_t *meet_launches, int64_t *launches, int32_t *waves,
                       int32_t *evictions, int64_t *arena_peak, int64_t *and_iters,
-                      int64_t *rows_transposed, double *words_ms, double *run_ms);
+                      int64_t *rows_transposed, double *words_ms, double *run_ms,
+                      double *sync_ms);
 
 /* Enables (1) or disables (0) per-kernel CUDA-event timing for later
  * searches on the calling thread. */

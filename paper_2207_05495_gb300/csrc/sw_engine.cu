@@ -43,6 +43,7 @@ struct Stats {
     int64_t pairs = 0, candidates = 0;
     int32_t iterations = 0;
     double meet_ms = 0, expand_ms = 0, compact_ms = 0, words_ms = 0, run_ms = 0;
+    double sync_ms = 0;  // host time spent waiting for the stream inside the search
     int32_t meet_launches = 0;
     int64_t and_iters = 0;  // bitmap meet: warp-wide AND steps
     int64_t rows_transposed = 0;  // bitmap meet: backward rows transposed into shared memory
@@ -241,6 +242,7 @@ struct Layout {
     // pools
     uint64_t *sets, *link;
     uint32_t *perm;  // forward levels: canonical position of the i-th set by cardinality
+    uint4 *rec;      // forward sets: first seven states and cardinality
     int64_t cap_sets;
     uint64_t *table;
     int64_t cap_table;
@@ -321,7 +323,7 @@ bool carve(void *ws, size_t bytes, int W, int32_t count, int64_t delta_elems, La
     if (rest < 256 * 1024) return false;
     rest -= 16 * 1024;
     // bytes: sets 55%, table 25%, candidates 20%
-    double set_b = 8.0 * W + 12, cand_b = 8.0 * W + 8 + 1 + 12.0 / kScanBlock;
+    double set_b = 8.0 * W + 28, cand_b = 8.0 * W + 8 + 1 + 12.0 / kScanBlock;
     int64_t S = (int64_t)(0.55 * rest / set_b);
     int64_t T = (int64_t)(0.25 * rest / 8.0);
     int64_t C = (int64_t)(0.20 * rest / cand_b);
@@ -331,6 +333,7 @@ bool carve(void *ws, size_t bytes, int W, int32_t count, int64_t delta_elems, La
     L.sets = cv.take<uint64_t>((size_t)S * W);
     L.link = cv.take<uint64_t>((size_t)S);
     L.perm = cv.take<uint32_t>((size_t)S);
+    L.rec = cv.take<uint4>((size_t)S);
     L.table = cv.take<uint64_t>((size_t)T);
     L.cand_sets = cv.take<uint64_t>((size_t)C * W);
     L.cand_slot = cv.take<int64_t>((size_t)C);
@@ -427,7 +430,7 @@ cudaError_t launch_meet_r(const MeetJob *jobs, int njobs, const int64_t *ntiles,
 
 template <int W>
 cudaError_t launch_meet_bm(const MeetJob *jobs, int njobs, const int64_t *ntiles, int tf_rows, const uint64_t *sets,
-                           const uint32_t *perm, unsigned long long *best, unsigned long long *pairs, unsigned long long *iters,
+                           const uint32_t *perm, const uint4 *rec, unsigned long long *best, unsigned long long *pairs, unsigned long long *iters,
                            unsigned long long *rows, const int32_t *meta, cudaStream_t st) {
     constexpr int NT = kBmThreads;
     auto kern = k_meet_bm<W, NT>;
@@ -441,7 +444,8 @@ cudaError_t launch_meet_bm(const MeetJob *jobs, int njobs, const int64_t *ntiles
     int per_sm = 0;
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, NT, smem);
     int64_t grid = (int64_t)sm_count() * std::max(per_sm, 1);
-    kern<<<(unsigned)grid, NT, smem, st>>>(jobs, njobs, ntiles, tf_rows, sets, perm, best, pairs, iters, rows, meta);
+    kern<<<(unsigned)grid, NT, smem, st>>>(jobs, njobs, ntiles, tf_rows, sets, perm, rec, best, pairs, iters, rows,
+                                           meta);
     return cudaGetLastError();
 }
 
@@ -459,7 +463,7 @@ struct Ops {
         for (int b = 0; b < nj; b += 65535) {
             dim3 grid((unsigned)((nmax + 1 + 255) / 256), (unsigned)std::min(65535, nj - b));
             g_stats.launches++;
-            k_roots<W><<<grid, 256, 0, st>>>(j + b, L.sets, L.link, L.perm, L.table, L.status);
+            k_roots<W><<<grid, 256, 0, st>>>(j + b, L.sets, L.link, L.perm, L.rec, L.table, L.status);
         }
         return cudaGetLastError();
     }
@@ -489,7 +493,7 @@ struct Ops {
         k_ge<<<(unsigned)nj, 32, 0, st>>>(jobs, HN, L.hist, L.cursor, L.meta);
         k_compact<W><<<(unsigned)nblocks, kScanThreads, 0, st>>>(jobs, nj, ncand, L.flag, L.block_off, L.cand_sets,
                                                                  L.cand_slot, L.table, L.sets, L.link, L.perm,
-                                                                 L.cursor);
+                                                                 L.rec, L.cursor);
         k_job_counts<<<(unsigned)((nj + 255) / 256), 256, 0, st>>>(jobs, nj, nblocks, L.block_off, L.counts);
         return cudaGetLastError();
     }
@@ -499,8 +503,8 @@ struct Ops {
         k_meet_prep<<<1, 1024, 0, st>>>(jobs, nj, L.counts, TF, c.tb, L.ntiles);
         const int64_t *ntiles = L.ntiles;
         if (c.algo == 0)
-            return launch_meet_bm<W>(jobs, nj, ntiles, c.tf_rows, L.sets, L.perm, L.best, L.pairs, L.pairs + 1,
-                                     L.pairs + 2, L.meta, st);
+            return launch_meet_bm<W>(jobs, nj, ntiles, c.tf_rows, L.sets, L.perm, L.rec, L.best, L.pairs,
+                                     L.pairs + 1, L.pairs + 2, L.meta, st);
         switch (c.R) {
             case 1:
                 if constexpr (W >= 3) return launch_meet_r<W, 1>(jobs, nj, ntiles, c.tb, L.sets, L.best, L.pairs, st);
@@ -583,6 +587,14 @@ float elapsed(cudaEvent_t a, cudaEvent_t b) {
     } while (0)
 
 int64_t round_up(int64_t x, int64_t m) { return (x + m - 1) / m * m; }
+
+// cudaStreamSynchronize, with the wait added to the search's statistics.
+cudaError_t wait_stream(cudaStream_t st) {
+    auto t0 = std::chrono::steady_clock::now();
+    cudaError_t e = cudaStreamSynchronize(st);
+    g_stats.sync_ms += std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+    return e;
+}
 
 // ---------------------------------------------------------------- the search engine
 
@@ -714,7 +726,7 @@ struct Engine {
         if (rc) return rc;
         CK(ops.fill(d_fj, 2 * nj, maxlen, L, st));
         CK(ops.roots(d_rj, nj, nmax, L, st));
-        CK(cudaStreamSynchronize(st));  // the staging buffer is reused next
+        CK(wait_stream(st));  // the staging buffer is reused next
         return SW_OK;
     }
 
@@ -870,7 +882,7 @@ struct Engine {
         CK(cudaMemcpyAsync(d_status, L.status, sizeof(uint32_t), cudaMemcpyDeviceToHost, st));
         CK(cudaMemcpyAsync(d_best, L.best, nj * sizeof(unsigned long long), cudaMemcpyDeviceToHost, st));
         CK(cudaMemcpyAsync(d_pairs, L.pairs, 3 * sizeof(unsigned long long), cudaMemcpyDeviceToHost, st));
-        CK(cudaStreamSynchronize(st));
+        CK(wait_stream(st));
         if (g_timing) {
             g_stats.expand_ms += elapsed(g_ev.ev[0], g_ev.ev[1]);
             g_stats.compact_ms += elapsed(g_ev.ev[1], g_ev.ev[2]);
@@ -973,7 +985,7 @@ struct Engine {
                 if (!hwd) return SW_ECUDA;
                 CK(cudaMemcpyAsync(hwd, L.word_area, (size_t)area, cudaMemcpyDeviceToHost, st));
             }
-            CK(cudaStreamSynchronize(st));
+            CK(wait_stream(st));
             if (g_timing) g_stats.words_ms += elapsed(g_ev.ev[5], g_ev.ev[6]);
             for (int t = 0; t < nw; ++t) {
                 Inst &x = I[wj[t].pad];
@@ -1469,7 +1481,7 @@ int32_t sw_batch_device(int32_t count, const int32_t *n, const int32_t *k, const
 int32_t sw_last_stats(int64_t *pairs, int64_t *candidates, int32_t *iterations, double *meet_ms,
                       double *expand_ms, double *compact_ms, int32_t *meet_launches, int64_t *launches,
                       int32_t *waves, int32_t *evictions, int64_t *arena_peak, int64_t *and_iters,
-                      int64_t *rows_transposed, double *words_ms, double *run_ms) {
+                      int64_t *rows_transposed, double *words_ms, double *run_ms, double *sync_ms) {
     if (pairs) *pairs = g_stats.pairs;
     if (candidates) *candidates = g_stats.candidates;
     if (iterations) *iterations = g_stats.iterations;
@@ -1485,6 +1497,7 @@ int32_t sw_last_stats(int64_t *pairs, int64_t *candidates, int32_t *iterations, 
     if (rows_transposed) *rows_transposed = g_stats.rows_transposed;
     if (words_ms) *words_ms = g_stats.words_ms;
     if (run_ms) *run_ms = g_stats.run_ms;
+    if (sync_ms) *sync_ms = g_stats.sync_ms;
     return SW_OK;
 }
 

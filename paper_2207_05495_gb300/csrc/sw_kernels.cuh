@@ -249,6 +249,28 @@ __device__ __forceinline__ void insert_stored(uint64_t *table, int64_t tab_off, 
     atomicOr(status, kStatusTableFull);
 }
 
+// The meet kernel's record of a forward set: its first seven states and its
+// cardinality as 16-bit fields (x: s0 | s1 << 16, y: s2 | s3 << 16,
+// z: s4 | s5 << 16, w: s6 | card << 16; missing states are 0xFFFF).
+template <int W>
+__device__ __forceinline__ uint4 row_record(const uint64_t (&s)[W]) {
+    uint32_t f[8];
+#pragma unroll
+    for (int i = 0; i < 7; ++i) f[i] = 0xFFFFu;
+    int card = 0, got = 0;
+#pragma unroll
+    for (int w = 0; w < W; ++w) {
+        uint64_t b = s[w];
+        card += __popcll(b);
+        while (b && got < 7) {
+            f[got++] = (uint32_t)(w * 64 + __ffsll((long long)b) - 1);
+            b &= b - 1;
+        }
+    }
+    f[7] = (uint32_t)card;
+    return make_uint4(f[0] | (f[1] << 16), f[2] | (f[3] << 16), f[4] | (f[5] << 16), f[6] | (f[7] << 16));
+}
+
 // ------------------------------------------------------------ roots, fill, rehash
 
 // F_0 = {Q} and B_0 = the n singletons of each new instance (Alg. 1,
@@ -256,8 +278,8 @@ __device__ __forceinline__ void insert_stored(uint64_t *table, int64_t tab_off, 
 // set; blockIdx.y = instance.
 template <int W>
 __global__ void k_roots(const RootJob *__restrict__ jobs, uint64_t *__restrict__ sets,
-                        uint64_t *__restrict__ link, uint32_t *__restrict__ perm, uint64_t *table,
-                        uint32_t *status) {
+                        uint64_t *__restrict__ link, uint32_t *__restrict__ perm, uint4 *__restrict__ rec,
+                        uint64_t *table, uint32_t *status) {
     const RootJob J = jobs[blockIdx.y];
     for (int t = blockIdx.x * blockDim.x + threadIdx.x; t <= J.n; t += gridDim.x * blockDim.x) {
         uint64_t s[W];
@@ -273,6 +295,7 @@ __global__ void k_roots(const RootJob *__restrict__ jobs, uint64_t *__restrict__
             dir = 0;
             link[g] = ~0ull;
             perm[g] = 0;
+            rec[g] = row_record<W>(s);
         } else {
             int q = t - 1;
 #pragma unroll
@@ -507,7 +530,8 @@ __global__ void __launch_bounds__(kScanThreads) k_compact(
     const ExpandJob *__restrict__ jobs, int njobs, int64_t ncand, const uint8_t *__restrict__ flag,
     const uint64_t *__restrict__ block_off, const uint64_t *__restrict__ cand_sets,
     const int64_t *__restrict__ cand_slot, uint64_t *__restrict__ table, uint64_t *__restrict__ sets,
-    uint64_t *__restrict__ link, uint32_t *__restrict__ perm, uint32_t *__restrict__ cursor) {
+    uint64_t *__restrict__ link, uint32_t *__restrict__ perm, uint4 *__restrict__ rec,
+    uint32_t *__restrict__ cursor) {
     constexpr int IPT = kScanBlock / kScanThreads;
     constexpr int HN = card_slots(W);
     int64_t base = (int64_t)blockIdx.x * kScanBlock + threadIdx.x * IPT;
@@ -575,8 +599,13 @@ __global__ void __launch_bounds__(kScanThreads) k_compact(
         if (!f[i]) continue;
         int64_t c = base + i;
         int64_t g = J.dest_off + (int64_t)(rank - first);
+        uint64_t t[W];
 #pragma unroll
-        for (int w = 0; w < W; ++w) sets[g * W + w] = cand_sets[c * W + w];
+        for (int w = 0; w < W; ++w) {
+            t[w] = cand_sets[c * W + w];
+            sets[g * W + w] = t[w];
+        }
+        rec[g] = row_record<W>(t);
         int64_t local = c - J.cand_off;
         int64_t p = local / J.k;
         link[g] = ((uint64_t)(J.parent_off + p) << 8) | (uint64_t)(local - p * J.k);
@@ -773,6 +802,7 @@ __global__ void __launch_bounds__(NT) k_meet_bm(const MeetJob *__restrict__ jobs
                                                 const int64_t *__restrict__ ntiles_p, int tf_rows,
                                                 const uint64_t *__restrict__ sets,
                                                 const uint32_t *__restrict__ perm,
+                                                const uint4 *__restrict__ rec,
                                                 unsigned long long *best, unsigned long long *pairs_done,
                                                 unsigned long long *and_iters,
                                                 unsigned long long *rows_transposed,
@@ -806,9 +836,7 @@ __global__ void __launch_bounds__(NT) k_meet_bm(const MeetJob *__restrict__ jobs
             int skip = 0;
             if (J.ge_off >= 0) {
                 const uint32_t f_first = perm[J.f_off + tf * tf_rows];
-                int card = 0;
-#pragma unroll
-                for (int w = 0; w < W; ++w) card += __popcll(sets[(J.f_off + f_first) * W + w]);
+                const int card = (int)(rec[J.f_off + f_first].w >> 16);
                 skip = b0 >= (int64_t)meta[J.ge_off + min(card, HN - 1)];
             }
             s_best = *(volatile unsigned long long *)(best + J.slot);
@@ -847,31 +875,25 @@ __global__ void __launch_bounds__(NT) k_meet_bm(const MeetJob *__restrict__ jobs
         const int32_t *ge = J.ge_off >= 0 ? meta + J.ge_off : nullptr;
         int64_t i = i0 + warp;
         uint32_t f = 0;
-        uint64_t x[W];
+        uint4 r = make_uint4(0, 0, 0, 0);
         if (i < i1) {
             f = __ldg(perm + J.f_off + i);
-            load_set<W>(sets + (J.f_off + f) * W, x);
+            r = __ldg(rec + J.f_off + f);
         }
         for (; i < i1; i += NW) {
             uint32_t fn = 0;  // prefetch the warp's next row
-            uint64_t xn[W];
+            uint4 rn = make_uint4(0, 0, 0, 0);
             if (i + NW < i1) {
                 fn = __ldg(perm + J.f_off + i + NW);
-                load_set<W>(sets + (J.f_off + fn) * W, xn);
+                rn = __ldg(rec + J.f_off + fn);
             }
             // lane 0 reads the shared best; the whole warp follows its decision
             int pass = (int64_t)(*(volatile unsigned long long *)&s_best >> 32) <= (int64_t)f;
             // only the backward sets with at least |X| states can contain X
-            int card = 0;
-#pragma unroll
-            for (int w = 0; w < W; ++w) card += __popcll(x[w]);
+            const int card = (int)(r.w >> 16);
             int64_t end = ge ? (int64_t)__ldg(ge + min(card, HN - 1)) : J.b_cnt;
-            int rows = (int)max((int64_t)0, min((int64_t)nb, end - b0));
-            if (end <= b0) {  // later rows have at least as many states: none fits here
-#pragma unroll
-                for (int w = 0; w < W; ++w) x[w] = xn[w];
-                break;
-            }
+            if (end <= b0) break;  // later rows have at least as many states: none fits here
+            int rows = (int)min((int64_t)nb, end - b0);
             if (!__shfl_sync(0xffffffffu, pass, 0)) {
                 uint64_t acc[LW];
 #pragma unroll
@@ -880,28 +902,51 @@ __global__ void __launch_bounds__(NT) k_meet_bm(const MeetJob *__restrict__ jobs
                     acc[j] = lim >= 64 ? ~0ull : (lim > 0 ? ((1ull << lim) - 1) : 0ull);
                 }
                 bool alive = true;
+                uint32_t steps = 0;
+                // one AND step with the bitmap of state q; the first three
+                // steps skip the vote (a chunk almost never empties that soon)
+                auto step = [&](int q, bool vote) {
+                    const uint32_t *p = sT + q * G::kWords + ((lane ^ (q & 31)) * G::kUnit);
+                    uint64_t any;
+                    if constexpr (LW == 2) {
+                        uint4 v = *reinterpret_cast<const uint4 *>(p);
+                        acc[0] &= ((uint64_t)v.y << 32) | v.x;
+                        acc[LW - 1] &= ((uint64_t)v.w << 32) | v.z;
+                        any = acc[0] | acc[LW - 1];
+                    } else {
+                        uint2 v = *reinterpret_cast<const uint2 *>(p);
+                        acc[0] &= ((uint64_t)v.y << 32) | v.x;
+                        any = acc[0];
+                    }
+                    ++steps;
+                    if (vote) alive = __any_sync(0xffffffffu, any != 0);
+                };
+                const uint32_t rw[4] = {r.x, r.y, r.z, r.w};
+                const int listed = min(card, 7);
 #pragma unroll
-                for (int h = 0; h < 2 * W; ++h) {
-                    uint32_t bits = (h & 1) ? (uint32_t)(x[h >> 1] >> 32) : (uint32_t)x[h >> 1];
-                    while (bits && alive) {
-                        const int q = 32 * h + __ffs(bits) - 1;
-                        bits &= bits - 1;
-                        const uint32_t *p = sT + q * G::kWords + ((lane ^ (q & 31)) * G::kUnit);
-                        uint64_t any;
-                        if constexpr (LW == 2) {
-                            uint4 v = *reinterpret_cast<const uint4 *>(p);
-                            acc[0] &= ((uint64_t)v.y << 32) | v.x;
-                            acc[LW - 1] &= ((uint64_t)v.w << 32) | v.z;
-                            any = acc[0] | acc[LW - 1];
-                        } else {
-                            uint2 v = *reinterpret_cast<const uint2 *>(p);
-                            acc[0] &= ((uint64_t)v.y << 32) | v.x;
-                            any = acc[0];
+                for (int t = 0; t < 7; ++t) {
+                    if (t >= listed || !alive) break;
+                    step((int)((rw[t >> 1] >> ((t & 1) * 16)) & 0xFFFFu), t >= 2 || t == listed - 1);
+                }
+                if (alive && card > 7) {
+                    // the states after the seventh, from the set itself
+                    const int s6 = (int)(r.w & 0xFFFFu);
+                    uint64_t x[W];
+                    load_set<W>(sets + (J.f_off + f) * W, x);
+#pragma unroll
+                    for (int h = 0; h < 2 * W; ++h) {
+                        uint32_t bits = (h & 1) ? (uint32_t)(x[h >> 1] >> 32) : (uint32_t)x[h >> 1];
+                        const int lo = 32 * h;
+                        if (s6 >= lo + 31) bits = 0;
+                        else if (s6 >= lo) bits &= ~((2u << (s6 - lo)) - 1u);
+                        while (bits && alive) {
+                            const int q = lo + __ffs(bits) - 1;
+                            bits &= bits - 1;
+                            step(q, true);
                         }
-                        ++my_iters;
-                        alive = __any_sync(0xffffffffu, any != 0);
                     }
                 }
+                my_iters += steps;
                 my_pairs += (unsigned long long)rows;
                 if (alive) {  // every state of X processed: X lies inside the surviving sets
                     uint64_t any = 0;
@@ -922,8 +967,7 @@ __global__ void __launch_bounds__(NT) k_meet_bm(const MeetJob *__restrict__ jobs
                 }
             }
             f = fn;
-#pragma unroll
-            for (int w = 0; w < W; ++w) x[w] = xn[w];
+            r = rn;
         }
         __syncthreads();
     }
