@@ -236,6 +236,7 @@ struct Layout {
     int64_t word_area_cap;
     uint16_t *delta16;
     int64_t delta_cap;
+    uint64_t *pre;            // preimage tables: [delta entry][W] bitsets
     uint32_t *hist, *cursor;  // per job: survivor cardinalities, bucket cursors
     int32_t *meta;            // pool of backward levels' cardinality tables
     int64_t cap_meta;
@@ -292,6 +293,7 @@ size_t small_area_bytes(int32_t count, int64_t delta_elems, int W = 9) {
     add(3 * sizeof(unsigned long long));
     add((size_t)word_area_for(count));
     add((size_t)std::max<int64_t>(delta_elems, 1) * sizeof(uint16_t));
+    add((size_t)std::max<int64_t>(delta_elems, 1) * W * sizeof(uint64_t));
     add(2 * c * card_slots(W) * sizeof(uint32_t));
     add((size_t)meta_cap_for(count, W) * sizeof(int32_t));
     return b;
@@ -314,6 +316,7 @@ bool carve(void *ws, size_t bytes, int W, int32_t count, int64_t delta_elems, La
     L.word_area = cv.take<uint8_t>((size_t)L.word_area_cap);
     L.delta_cap = std::max<int64_t>(delta_elems, 1);
     L.delta16 = cv.take<uint16_t>((size_t)L.delta_cap);
+    L.pre = cv.take<uint64_t>((size_t)L.delta_cap * W);
     L.hist = cv.take<uint32_t>(c * card_slots(W));
     L.cursor = cv.take<uint32_t>(c * card_slots(W));
     L.cap_meta = meta_cap_for(count, W);
@@ -467,6 +470,15 @@ struct Ops {
         }
         return cudaGetLastError();
     }
+    static cudaError_t pre(const PreJob *j, int nj, int64_t maxlen, const Layout &L, cudaStream_t st) {
+        for (int b = 0; b < nj; b += 65535) {
+            dim3 grid((unsigned)std::min<int64_t>((maxlen * W + 255) / 256, 64), (unsigned)std::min(65535, nj - b));
+            g_stats.launches += 2;
+            k_pre_clear<W><<<grid, 256, 0, st>>>(j + b, L.pre);
+            k_pre_fill<W><<<grid, 256, 0, st>>>(j + b, L.delta16, L.pre);
+        }
+        return cudaGetLastError();
+    }
     static cudaError_t rehash(const RehashSeg *segs, int nseg, int64_t total, const Layout &L, cudaStream_t st) {
         int64_t blocks = std::min<int64_t>((total + 255) / 256, (int64_t)sm_count() * 16);
         g_stats.launches++;
@@ -478,7 +490,7 @@ struct Ops {
         int64_t blocks = std::min<int64_t>((ncand + 255) / 256, (int64_t)sm_count() * 16);
         g_stats.launches++;
         k_expand<W><<<(unsigned)std::max<int64_t>(blocks, 1), 256, 0, st>>>(
-            jobs, nj, ncand, L.delta16, L.sets, L.table, L.cand_sets, L.cand_slot, L.status);
+            jobs, nj, ncand, L.delta16, L.pre, L.sets, L.table, L.cand_sets, L.cand_slot, L.status);
         return cudaGetLastError();
     }
     static cudaError_t compact(const ExpandJob *jobs, int nj, int64_t ncand, const Layout &L, cudaStream_t st) {
@@ -527,6 +539,7 @@ struct Ops {
 };
 
 struct OpTable {
+    cudaError_t (*pre)(const PreJob *, int, int64_t, const Layout &, cudaStream_t);
     cudaError_t (*fill)(const FillJob *, int, int64_t, const Layout &, cudaStream_t);
     cudaError_t (*roots)(const RootJob *, int, int, const Layout &, cudaStream_t);
     cudaError_t (*rehash)(const RehashSeg *, int, int64_t, const Layout &, cudaStream_t);
@@ -538,7 +551,7 @@ struct OpTable {
 
 template <int W>
 OpTable make_ops() {
-    return {&Ops<W>::fill, &Ops<W>::roots, &Ops<W>::rehash, &Ops<W>::expand, &Ops<W>::compact, &Ops<W>::meet,
+    return {&Ops<W>::pre, &Ops<W>::fill, &Ops<W>::roots, &Ops<W>::rehash, &Ops<W>::expand, &Ops<W>::compact, &Ops<W>::meet,
             &Ops<W>::words};
 }
 
@@ -673,7 +686,7 @@ struct Engine {
         *taken = 0;
         if (!stage_begin()) return SW_ECUDA;
         std::vector<int> ok;
-        size_t cap_jobs = (L.mirror_bytes / 2) / (sizeof(RootJob) + 2 * sizeof(FillJob));
+        size_t cap_jobs = (L.mirror_bytes / 2) / (sizeof(RootJob) + 2 * sizeof(FillJob) + sizeof(PreJob));
         for (size_t t = first; t < ids.size() && ok.size() < cap_jobs; ++t) {
             Inst &x = I[ids[t]];
             int64_t tc0 = 64, tc1 = round_up(4 * (int64_t)x.n, 64);
@@ -707,9 +720,12 @@ struct Engine {
         int nj = (int)ok.size();
         RootJob *d_rj;
         FillJob *d_fj;
+        PreJob *d_pj;
         RootJob *rj = stg.take<RootJob>(nj, &d_rj);
         FillJob *fj = stg.take<FillJob>(2 * nj, &d_fj);
+        PreJob *pj = stg.take<PreJob>(nj, &d_pj);
         if (!stg.ok) return SW_EINTERNAL;
+        int64_t maxkn = 1;
         int nmax = 1;
         int64_t maxlen = 1;
         for (int t = 0; t < nj; ++t) {
@@ -718,12 +734,15 @@ struct Engine {
                             {x.tab_cap[0], x.tab_cap[1]}, x.n, 0};
             fj[2 * t] = FillJob{x.tab_off[0], x.tab_cap[0]};
             fj[2 * t + 1] = FillJob{x.tab_off[1], x.tab_cap[1]};
+            pj[t] = PreJob{x.delta_off, x.n, x.k};
+            maxkn = std::max(maxkn, (int64_t)x.n * x.k);
             nmax = std::max(nmax, x.n);
             maxlen = std::max(maxlen, x.tab_cap[1]);
             active.push_back(ok[t]);
         }
         int rc = stage_flush();
         if (rc) return rc;
+        CK(ops.pre(d_pj, nj, maxkn, L, st));
         CK(ops.fill(d_fj, 2 * nj, maxlen, L, st));
         CK(ops.roots(d_rj, nj, nmax, L, st));
         CK(wait_stream(st));  // the staging buffer is reused next

@@ -192,17 +192,25 @@ __device__ __forceinline__ void image(const uint64_t (&S)[W], const uint16_t *__
     }
 }
 
-// Preimage delta^{-1}(S, a) (Section 2): state p is in it iff S holds delta(p, a).
+// Preimage delta^{-1}(S, a) (Section 2): state p is in it iff S holds
+// delta(p, a).  pre_a holds, for every state t, the bitset
+// delta^{-1}({t}, a) (W words), so the preimage is the union of those rows
+// over the states of S.
 template <int W>
-__device__ __forceinline__ void preimage(const uint64_t (&S)[W], const uint16_t *__restrict__ da,
-                                         int n, uint64_t (&T)[W]) {
+__device__ __forceinline__ void preimage(const uint64_t (&S)[W], const uint64_t *__restrict__ pre_a,
+                                         uint64_t (&T)[W]) {
+#pragma unroll
+    for (int w = 0; w < W; ++w) T[w] = 0;
 #pragma unroll
     for (int w = 0; w < W; ++w) {
-        uint64_t acc = 0;
-        int base = w * 64;
-        int lim = n - base < 64 ? n - base : 64;
-        for (int b = 0; b < lim; ++b) acc |= (uint64_t)get_bit<W>(S, __ldg(da + base + b)) << b;
-        T[w] = acc;
+        uint64_t s = S[w];
+        while (s) {
+            const int t = w * 64 + __ffsll((long long)s) - 1;
+            s &= s - 1;
+            const uint64_t *row = pre_a + (int64_t)t * W;
+#pragma unroll
+            for (int v = 0; v < W; ++v) T[v] |= __ldg(row + v);
+        }
     }
 }
 
@@ -349,8 +357,8 @@ __global__ void k_rehash(const RehashSeg *__restrict__ segs, int nseg, int64_t t
 template <int W>
 __global__ void __launch_bounds__(256) k_expand(
     const ExpandJob *__restrict__ jobs, int njobs, int64_t ncand, const uint16_t *__restrict__ delta16,
-    const uint64_t *__restrict__ sets, uint64_t *table, uint64_t *cand_sets, int64_t *__restrict__ cand_slot,
-    uint32_t *status) {
+    const uint64_t *__restrict__ pre, const uint64_t *__restrict__ sets, uint64_t *table, uint64_t *cand_sets,
+    int64_t *__restrict__ cand_slot, uint32_t *status) {
     for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < ncand;
          c += (int64_t)gridDim.x * blockDim.x) {
         const ExpandJob &J = jobs[find_job_expand(jobs, njobs, c)];
@@ -363,10 +371,9 @@ __global__ void __launch_bounds__(256) k_expand(
         int a = (int)(local - p * J.k);
         uint64_t S[W], T[W];
         load_set<W>(sets + (J.parent_off + p) * W, S);
-        const uint16_t *da = delta16 + J.delta_off + (int64_t)a * J.n;
         const uint32_t dir = (uint32_t)J.dir;
-        if (dir == 0) image<W>(S, da, T);
-        else preimage<W>(S, da, J.n, T);
+        if (dir == 0) image<W>(S, delta16 + J.delta_off + (int64_t)a * J.n, T);
+        else preimage<W>(S, pre + (J.delta_off + (int64_t)a * J.n) * W, T);
         bool empty = true;
 #pragma unroll
         for (int w = 0; w < W; ++w) empty &= (T[w] == 0);
@@ -874,33 +881,41 @@ __global__ void __launch_bounds__(NT) k_meet_bm(const MeetJob *__restrict__ jobs
         //    matters, so rows at or past the best f found are passed over
         const int32_t *ge = J.ge_off >= 0 ? meta + J.ge_off : nullptr;
         int64_t i = i0 + warp;
-        uint32_t f = 0;
+        uint32_t f = 0, fn = 0;
         uint4 r = make_uint4(0, 0, 0, 0);
         if (i < i1) {
             f = __ldg(perm + J.f_off + i);
             r = __ldg(rec + J.f_off + f);
         }
+        if (i + NW < i1) fn = __ldg(perm + J.f_off + i + NW);
+        int last_card = -1, rows = 0;
+        uint64_t mask[LW];
         for (; i < i1; i += NW) {
-            uint32_t fn = 0;  // prefetch the warp's next row
+            // prefetch: the record of the next row, the index of the one after
+            uint32_t fnn = 0;
             uint4 rn = make_uint4(0, 0, 0, 0);
-            if (i + NW < i1) {
-                fn = __ldg(perm + J.f_off + i + NW);
-                rn = __ldg(rec + J.f_off + fn);
-            }
+            if (i + 2 * NW < i1) fnn = __ldg(perm + J.f_off + i + 2 * NW);
+            if (i + NW < i1) rn = __ldg(rec + J.f_off + fn);
             // lane 0 reads the shared best; the whole warp follows its decision
             int pass = (int64_t)(*(volatile unsigned long long *)&s_best >> 32) <= (int64_t)f;
-            // only the backward sets with at least |X| states can contain X
+            // only the backward sets with at least |X| states can contain X;
+            // rows come in increasing cardinality, so the bound changes rarely
             const int card = (int)(r.w >> 16);
-            int64_t end = ge ? (int64_t)__ldg(ge + min(card, HN - 1)) : J.b_cnt;
-            if (end <= b0) break;  // later rows have at least as many states: none fits here
-            int rows = (int)min((int64_t)nb, end - b0);
-            if (!__shfl_sync(0xffffffffu, pass, 0)) {
-                uint64_t acc[LW];
+            if (card != last_card) {
+                int64_t end = ge ? (int64_t)__ldg(ge + min(card, HN - 1)) : J.b_cnt;
+                if (end <= b0) break;  // later rows have at least as many states: none fits here
+                rows = (int)min((int64_t)nb, end - b0);
 #pragma unroll
                 for (int j = 0; j < LW; ++j) {
                     int lim = rows - 64 * (LW * lane + j);
-                    acc[j] = lim >= 64 ? ~0ull : (lim > 0 ? ((1ull << lim) - 1) : 0ull);
+                    mask[j] = lim >= 64 ? ~0ull : (lim > 0 ? ((1ull << lim) - 1) : 0ull);
                 }
+                last_card = card;
+            }
+            if (!__shfl_sync(0xffffffffu, pass, 0)) {
+                uint64_t acc[LW];
+#pragma unroll
+                for (int j = 0; j < LW; ++j) acc[j] = mask[j];
                 bool alive = true;
                 uint32_t steps = 0;
                 // one AND step with the bitmap of state q; the first three
@@ -968,6 +983,7 @@ __global__ void __launch_bounds__(NT) k_meet_bm(const MeetJob *__restrict__ jobs
             }
             f = fn;
             r = rn;
+            fn = fnn;
         }
         __syncthreads();
     }
@@ -1082,6 +1098,35 @@ __global__ void __launch_bounds__(NT) k_words(const WordJob *__restrict__ jobs,
             if (pc != 1) st = kStatusVerifyFail;
         }
         word_status[J.slot] = st;
+    }
+}
+
+// Preimage tables of one instance per blockIdx.y: pre[(a*n + t)*W ..] is the
+// bitset {p : delta(p, a) = t}.  The rows are cleared first, then every
+// (a, p) sets its bit.
+struct PreJob {
+    int64_t delta_off;   // the instance's [k][n] entries; its table starts at delta_off * W
+    int32_t n, k;
+};
+
+template <int W>
+__global__ void k_pre_clear(const PreJob *__restrict__ jobs, uint64_t *__restrict__ pre) {
+    const PreJob J = jobs[blockIdx.y];
+    const int64_t len = (int64_t)J.k * J.n * W;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < len; i += (int64_t)gridDim.x * blockDim.x)
+        pre[J.delta_off * W + i] = 0;
+}
+
+template <int W>
+__global__ void k_pre_fill(const PreJob *__restrict__ jobs, const uint16_t *__restrict__ delta16,
+                           uint64_t *__restrict__ pre) {
+    const PreJob J = jobs[blockIdx.y];
+    const int64_t len = (int64_t)J.k * J.n;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < len; i += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t a = i / J.n, p = i - a * J.n;
+        const int t = delta16[J.delta_off + i];
+        atomicOr((unsigned long long *)(pre + (J.delta_off + a * J.n + t) * W + (p >> 6)),
+                 1ull << (p & 63));
     }
 }
 
