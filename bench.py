@@ -273,6 +273,8 @@ def main():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--count", type=int, default=0, help="use only the first COUNT instances (small cases)")
     ap.add_argument("--no-serve", action="store_true")
+    ap.add_argument("--opt", action="append", default=[],
+                    help="override a search option after tuning, e.g. --opt meet_lane_words=4")
     ap.add_argument("--serve-requests", type=int, default=1500)
     args = ap.parse_args()
 
@@ -318,7 +320,16 @@ def main():
     count = len(ds)
     from paper_2207_05495_gb300 import autotune
     tuned = autotune.apply(max((d.shape[1] + 63) // 64 for d in ds), int(ds[0].shape[0]))
-    cfg["options"] = tuned if tuned else "library defaults"
+    cfg["options"] = dict(tuned) if tuned else {}
+    if args.opt:
+        o = sw.sw_get_options()
+        for kv in args.opt:
+            k, v = kv.split("=")
+            setattr(o, k, type(getattr(o, k))(float(v)) if isinstance(getattr(o, k), float) else int(v))
+            cfg["options"][k] = v
+        sw.sw_set_options(o)
+    if not cfg["options"]:
+        cfg["options"] = "library defaults"
     ns = np.array([d.shape[1] for d in ds], np.int32)
     ks = np.array([d.shape[0] for d in ds], np.int32)
     W = int(max((int(n) + 63) // 64 for n in ns))
@@ -443,7 +454,9 @@ def main():
                                "compact": sum(s["compact_ms"] for s in stats) / len(stats),
                                "words": sum(s["words_ms"] for s in stats) / len(stats),
                                "host_wall": sum(s["run_ms"] for s in stats) / len(stats),
-                               "host_wait": sum(s["sync_ms"] for s in stats) / len(stats)},
+                               "host_wait": sum(s["sync_ms"] for s in stats) / len(stats),
+                               "host_select": sum(s["select_ms"] for s in stats) / len(stats),
+                               "host_update": sum(s["update_ms"] for s in stats) / len(stats)},
         "iterations_per_step": st["iterations"], "waves": st["waves"], "evictions": st["evictions"],
         "arena_peak_sets": st["arena_peak"],
         "one_at_a_time": {"value": m / one_s, "unit": "instances/s", "sample": f"first {m} instances",

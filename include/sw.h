@@ -203,13 +203,15 @@ int32_t sw_batch_device(int32_t count, const int32_t *n, const int32_t *k,
  *   run_ms:       host wall time of the whole search.
  *   sync_ms:      part of run_ms spent waiting for the stream; the rest is
  *                 host work between launches.
+ *   select_ms, update_ms: host time choosing each iteration's jobs and
+ *                 recording the levels they produced.
  */
 int32_t sw_last_stats(int64_t *pairs, int64_t *candidates, int32_t *iterations,
                       double *meet_ms, double *expand_ms, double *compact_ms,
                       int32_t *meet_launches, int64_t *launches, int32_t *waves,
                       int32_t *evictions, int64_t *arena_peak, int64_t *and_iters,
                       int64_t *rows_transposed, double *words_ms, double *run_ms,
-                      double *sync_ms);
+                      double *sync_ms, double *select_ms, double *update_ms);
 
 /* Enables (1) or disables (0) per-kernel CUDA-event timing for later
  * searches on the calling thread. */
@@ -227,6 +229,9 @@ void sw_set_timing(int32_t on);
  *   meet_b_tile:          direct test: backward sets per shared-memory tile
  *                         (even).
  *   meet_f_rows:          bitmap test: forward sets per tile (0 = 4096).
+ *   meet_lane_words:      bitmap test: 0 = default chunk (4096 backward
+ *                         sets for up to 192 states, else 2048); 4 = chunks
+ *                         of 8192 sets (up to 192 states only).
  *   dir_theta:            a forward step is taken when its predicted cost is
  *                         at most dir_theta times the backward step's.
  *   set_cost:             cost of producing one set, in pair tests (the
@@ -238,6 +243,7 @@ typedef struct sw_options {
     int32_t meet_rows_per_thread;
     int32_t meet_b_tile;
     int32_t meet_f_rows;
+    int32_t meet_lane_words;
     double dir_theta;
     double set_cost;
 } sw_options;

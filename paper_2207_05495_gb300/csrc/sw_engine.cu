@@ -44,6 +44,7 @@ struct Stats {
     int32_t iterations = 0;
     double meet_ms = 0, expand_ms = 0, compact_ms = 0, words_ms = 0, run_ms = 0;
     double sync_ms = 0;  // host time spent waiting for the stream inside the search
+    double select_ms = 0, update_ms = 0;  // host: choosing jobs, recording new levels
     int32_t meet_launches = 0;
     int64_t and_iters = 0;  // bitmap meet: warp-wide AND steps
     int64_t rows_transposed = 0;  // bitmap meet: backward rows transposed into shared memory
@@ -53,7 +54,7 @@ struct Stats {
 };
 
 thread_local int32_t g_last_error = SW_OK;
-thread_local sw_options g_opt = {0, 0, 0, 4096, 1.0, 8192.0};
+thread_local sw_options g_opt = {0, 0, 0, 4096, 0, 1.0, 8192.0};
 thread_local bool g_timing = false;
 thread_local Stats g_stats;
 // Set only while sw_reset_threshold_static runs: staging buffers then come
@@ -196,14 +197,20 @@ struct Pool {
 enum InstState { kWaiting = 0, kActive = 1, kDone = 2, kFailed = 3 };
 
 struct Level {
-    int64_t off, cnt, cap;  // arena index, sets, slots held in the set pool
-    int64_t ge = -1;        // backward: its cardinality table in the meta pool, or -1
+    int64_t off, cnt, cap;  // arena index, sets, slots reserved
+    int64_t ge = -1;        // backward: its cardinality table (int32 index into the set pool), or -1
+};
+
+// A run of set slots owned by one instance; levels are bump-allocated in it.
+struct Chunk {
+    int64_t off, cap, used;
 };
 
 struct Inst {
     int32_t n = 0, k = 0, orig = 0;
     int64_t delta_off = 0;
     std::vector<Level> lev[2];
+    std::vector<Chunk> chunks;
     int64_t tab_off[2] = {-1, -1}, tab_cap[2] = {0, 0}, stored[2] = {0, 0};
     double dupl[2] = {0.0, 0.0};
     int32_t state = kWaiting, code = SW_OK, r = -1;
@@ -212,10 +219,8 @@ struct Inst {
     std::vector<int64_t> sizes[2];         // level sizes of the finished search
     int64_t footprint() const {
         int64_t b = 0;
-        for (int d = 0; d < 2; ++d) {
-            for (auto &l : lev[d]) b += l.cap;
-            b += tab_cap[d] / 4;  // a table slot is a quarter of a set (W = 1) or less
-        }
+        for (auto &c : chunks) b += c.cap;
+        for (int d = 0; d < 2; ++d) b += tab_cap[d] / 4;  // a table slot is a quarter of a set (W = 1) or less
         return b;
     }
 };
@@ -238,8 +243,7 @@ struct Layout {
     int64_t delta_cap;
     uint64_t *pre;            // preimage tables: [delta entry][W] bitsets
     uint32_t *hist, *cursor;  // per job: survivor cardinalities, bucket cursors
-    int32_t *meta;            // pool of backward levels' cardinality tables
-    int64_t cap_meta;
+    int32_t *meta;            // the set pool as int32: backward levels' cardinality tables
     // pools
     uint64_t *sets, *link;
     uint32_t *perm;  // forward levels: canonical position of the i-th set by cardinality
@@ -277,8 +281,6 @@ struct Carver {
 size_t mirror_bytes_for(int32_t count) { return (size_t)std::max(count, 1) * 1024 + (1 << 20); }
 int64_t word_area_for(int32_t count) { return (int64_t)std::max<size_t>((size_t)std::max(count, 1) * 512, 1 << 20); }
 
-// room for the cardinality tables of about 48 backward levels per instance
-int64_t meta_cap_for(int32_t count, int W) { return (int64_t)(48 * std::max(count, 1) + 256) * card_slots(W); }
 
 size_t small_area_bytes(int32_t count, int64_t delta_elems, int W = 9) {
     size_t c = (size_t)std::max(count, 1);
@@ -295,7 +297,6 @@ size_t small_area_bytes(int32_t count, int64_t delta_elems, int W = 9) {
     add((size_t)std::max<int64_t>(delta_elems, 1) * sizeof(uint16_t));
     add((size_t)std::max<int64_t>(delta_elems, 1) * W * sizeof(uint64_t));
     add(2 * c * card_slots(W) * sizeof(uint32_t));
-    add((size_t)meta_cap_for(count, W) * sizeof(int32_t));
     return b;
 }
 
@@ -319,8 +320,6 @@ bool carve(void *ws, size_t bytes, int W, int32_t count, int64_t delta_elems, La
     L.pre = cv.take<uint64_t>((size_t)L.delta_cap * W);
     L.hist = cv.take<uint32_t>(c * card_slots(W));
     L.cursor = cv.take<uint32_t>(c * card_slots(W));
-    L.cap_meta = meta_cap_for(count, W);
-    L.meta = cv.take<int32_t>((size_t)L.cap_meta);
     if (!cv.ok) return false;
     size_t rest = cv.size - cv.used;
     if (rest < 256 * 1024) return false;
@@ -334,6 +333,7 @@ bool carve(void *ws, size_t bytes, int W, int32_t count, int64_t delta_elems, La
     if (S < 64 || T < 256 || C < kScanBlock) return false;
     int64_t nblocks = C / kScanBlock;
     L.sets = cv.take<uint64_t>((size_t)S * W);
+    L.meta = (int32_t *)L.sets;  // cardinality tables live in set slots
     L.link = cv.take<uint64_t>((size_t)S);
     L.perm = cv.take<uint32_t>((size_t)S);
     L.rec = cv.take<uint4>((size_t)S);
@@ -389,6 +389,7 @@ int default_btile(int W) { return std::max(64, (4096 / W) & ~1); }
 
 struct MeetCfg {
     int algo;     // 0 vertical bitmaps, 1 direct LOP3 test
+    int lw;       // bitmap test: 64-bit words of the running AND per lane
     int R, tb, nt;
     int tf_rows;  // forward rows per tile (bitmap kernel)
 };
@@ -406,7 +407,8 @@ MeetCfg meet_cfg(int W) {
     c.tb = std::min(tb, max_tb);
     c.nt = 256;
     c.algo = g_opt.meet_algo == 1 ? 1 : 0;
-    if (c.algo == 0) c.tb = bm_rows(W);
+    c.lw = g_opt.meet_lane_words == 4 && W <= 3 ? 4 : bm_lanes_words(W);
+    if (c.algo == 0) c.tb = 2048 * c.lw;
     c.tf_rows = g_opt.meet_f_rows > 0 ? g_opt.meet_f_rows : 4096;
     c.tf_rows = std::max(8, std::min(c.tf_rows, 1 << 20));
     return c;
@@ -431,13 +433,12 @@ cudaError_t launch_meet_r(const MeetJob *jobs, int njobs, const int64_t *ntiles,
     return cudaGetLastError();
 }
 
-template <int W>
+template <int W, int LW, int NT>
 cudaError_t launch_meet_bm(const MeetJob *jobs, int njobs, const int64_t *ntiles, int tf_rows, const uint64_t *sets,
                            const uint32_t *perm, const uint4 *rec, unsigned long long *best, unsigned long long *pairs, unsigned long long *iters,
                            unsigned long long *rows, const int32_t *meta, cudaStream_t st) {
-    constexpr int NT = kBmThreads;
-    auto kern = k_meet_bm<W, NT>;
-    size_t smem = (size_t)bm_smem_bytes(W);
+    auto kern = k_meet_bm<W, LW, NT>;
+    size_t smem = (size_t)bm_smem_bytes(W, LW);
     static thread_local bool configured = false;
     if (!configured) {
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -514,9 +515,15 @@ struct Ops {
         const int64_t TF = c.algo == 0 ? (int64_t)c.tf_rows : (int64_t)c.nt * c.R;
         k_meet_prep<<<1, 1024, 0, st>>>(jobs, nj, L.counts, TF, c.tb, L.ntiles);
         const int64_t *ntiles = L.ntiles;
-        if (c.algo == 0)
-            return launch_meet_bm<W>(jobs, nj, ntiles, c.tf_rows, L.sets, L.perm, L.rec, L.best, L.pairs,
-                                     L.pairs + 1, L.pairs + 2, L.meta, st);
+        if (c.algo == 0) {
+            if constexpr (W <= 3)
+                if (c.lw == 4)
+                    return launch_meet_bm<W, 4, 1024>(jobs, nj, ntiles, c.tf_rows, L.sets, L.perm, L.rec, L.best,
+                                                      L.pairs, L.pairs + 1, L.pairs + 2, L.meta, st);
+            return launch_meet_bm<W, bm_lanes_words(W), kBmThreads>(jobs, nj, ntiles, c.tf_rows, L.sets, L.perm,
+                                                                    L.rec, L.best, L.pairs, L.pairs + 1,
+                                                                    L.pairs + 2, L.meta, st);
+        }
         switch (c.R) {
             case 1:
                 if constexpr (W >= 3) return launch_meet_r<W, 1>(jobs, nj, ntiles, c.tb, L.sets, L.best, L.pairs, st);
@@ -621,7 +628,7 @@ struct Engine {
     Layout L;
     OpTable ops;
     MeetCfg mc;
-    Pool set_pool, tab_pool, meta_pool;
+    Pool set_pool, tab_pool;
     std::vector<Inst> &I;
     bool device_words = false;  // words go straight to the caller's device buffer
     uint8_t *out_words = nullptr;
@@ -633,7 +640,39 @@ struct Engine {
         mc = meet_cfg(W);
         set_pool.init(L.cap_sets);
         tab_pool.init(L.cap_table);
-        meta_pool.init(L.cap_meta);
+    }
+
+    // Set slots of a cardinality table (int32[card_slots(W)]) kept in the set pool.
+    int64_t ge_slots() const { return (card_slots(W) + 2 * W - 1) / (2 * W); }
+
+    // n contiguous set slots for instance x: from the end of its last chunk,
+    // else from a new chunk (room for about three more levels of this size
+    // when the pool allows); -1 when the pool has no room.
+    int64_t inst_alloc(Inst &x, int64_t n) {
+        if (n < 1) n = 1;
+        if (!x.chunks.empty()) {
+            Chunk &c = x.chunks.back();
+            if (c.cap - c.used >= n) {
+                int64_t off = c.off + c.used;
+                c.used += n;
+                return off;
+            }
+        }
+        int64_t want = std::max<int64_t>(4 * n, x.chunks.empty() ? 8 * ((int64_t)x.n + 1) : x.chunks.back().cap * 3 / 2);
+        int64_t off = set_pool.alloc(want);
+        if (off < 0) {
+            want = n;
+            off = set_pool.alloc(n);
+        }
+        if (off < 0) return -1;
+        x.chunks.push_back({off, want, n});
+        return off;
+    }
+
+    // Returns the unused end of x's most recent allocation [off, off + had).
+    void inst_shrink(Inst &x, int64_t off, int64_t had, int64_t keep) {
+        Chunk &c = x.chunks.back();
+        if (off + had == c.off + c.used) c.used -= had - keep;
     }
 
     bool stage_begin() {
@@ -658,11 +697,9 @@ struct Engine {
     }
 
     void release(Inst &x) {
+        for (auto &c : x.chunks) set_pool.release(c.off, c.cap);
+        x.chunks.clear();
         for (int d = 0; d < 2; ++d) {
-            for (auto &l : x.lev[d]) {
-                set_pool.release(l.off, l.cap);
-                if (l.ge >= 0) meta_pool.release(l.ge, card_slots(W));
-            }
             x.lev[d].clear();
             if (x.tab_off[d] >= 0) tab_pool.release(x.tab_off[d], x.tab_cap[d]);
             x.tab_off[d] = -1;
@@ -690,13 +727,14 @@ struct Engine {
         for (size_t t = first; t < ids.size() && ok.size() < cap_jobs; ++t) {
             Inst &x = I[ids[t]];
             int64_t tc0 = 64, tc1 = round_up(4 * (int64_t)x.n, 64);
-            int64_t f = set_pool.alloc(1);
-            int64_t b = f >= 0 ? set_pool.alloc(x.n) : -1;
+            x.chunks.clear();
+            int64_t f = inst_alloc(x, 1);
+            int64_t b = f >= 0 ? inst_alloc(x, x.n) : -1;
             int64_t t0 = b >= 0 ? tab_pool.alloc(tc0) : -1;
             int64_t t1 = t0 >= 0 ? tab_pool.alloc(tc1) : -1;
             if (t1 < 0) {
-                if (f >= 0) set_pool.release(f, 1);
-                if (b >= 0) set_pool.release(b, x.n);
+                for (auto &c : x.chunks) set_pool.release(c.off, c.cap);
+                x.chunks.clear();
                 if (t0 >= 0) tab_pool.release(t0, tc0);
                 break;
             }
@@ -752,6 +790,7 @@ struct Engine {
     // One iteration over the active instances.
     int iterate() {
         g_stats.iterations++;
+        auto t_sel = std::chrono::steady_clock::now();
         if (!stage_begin()) return SW_ECUDA;
         struct Sel {
             int id, d;
@@ -778,9 +817,14 @@ struct Engine {
                 nt = tab_pool.alloc(ntc);
                 if (nt < 0) continue;
             }
-            int64_t dest = set_pool.alloc(nc);
-            // a full table pool only costs the level its cardinality table
-            int64_t ge = (dest >= 0 && d == 1) ? meta_pool.alloc(card_slots(W)) : -1;
+            // the level's cardinality table (backward) and then the level
+            // itself, last in the chunk so that its unused end can be returned
+            int64_t ge = -1;
+            if (d == 1) {
+                int64_t gs = inst_alloc(x, ge_slots());
+                if (gs >= 0) ge = gs * 2 * W;  // int32 index into the set pool
+            }
+            int64_t dest = inst_alloc(x, nc);
             if (dest < 0) {
                 if (nt >= 0) tab_pool.release(nt, ntc);
                 continue;
@@ -877,6 +921,8 @@ struct Engine {
         }
         int rc = stage_flush();
         if (rc) return rc;
+        g_stats.select_ms +=
+            std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t_sel).count();
         g_stats.candidates += ncand;
         if (!fills.empty()) {
             CK(ops.fill(d_fill, (int)fills.size(), maxfill, L, st));
@@ -912,13 +958,14 @@ struct Engine {
         g_stats.and_iters += (int64_t)d_pairs[1];
         g_stats.rows_transposed += (int64_t)d_pairs[2];
         // new levels; return the unused tail of each destination
+        auto t_upd = std::chrono::steady_clock::now();
         std::vector<int> met;
         std::vector<unsigned long long> best;
         for (int t = 0; t < nj; ++t) {
             Sel &s = sel[t];
             Inst &x = I[s.id];
             int64_t c = (int64_t)down[t];
-            set_pool.release(s.dest + c, s.nc - c);
+            inst_shrink(x, s.dest, s.nc, c);
             x.lev[s.d].push_back({s.dest, c, c, s.ge});
             x.dupl[s.d] = 1.0 - (double)c / (double)s.nc;
             x.stored[s.d] += c;
@@ -929,6 +976,8 @@ struct Engine {
                 best.push_back(d_best[t]);
             }
         }
+        g_stats.update_ms +=
+            std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t_upd).count();
         if (!met.empty()) {
             rc = recover_words(met, best);
             if (rc) return rc;
@@ -1105,6 +1154,7 @@ struct sw_server {
     };
     std::deque<Sub> incoming;
     std::deque<int> queue;  // slots waiting for admission
+    std::vector<uint16_t> staged_delta;
     struct Done {
         uint64_t req;
         int32_t r, code;
@@ -1124,9 +1174,12 @@ struct sw_server {
 };
 
 int sw_server::admit_some() {
-    // take submissions into free slots (their delta tables go to the device)
+    // take submissions into free slots; their delta tables go to the device
+    // together (one staging buffer, one copy per request, no sync between)
     {
         std::lock_guard<std::mutex> lk(mu);
+        size_t bytes = 0;
+        std::vector<int> taken;
         while (!incoming.empty() && !free_slots.empty()) {
             Sub &sb = incoming.front();
             int64_t doff = delta_pool.alloc((int64_t)sb.n * sb.k);
@@ -1142,12 +1195,26 @@ int sw_server::admit_some() {
             x.word_cap = word_cap;
             slots[id] = x;
             req_of[id] = sb.req;
-            if (cudaMemcpyAsync(L.delta16 + doff, sb.delta.data(), sb.delta.size() * sizeof(uint16_t),
-                                cudaMemcpyHostToDevice, st) != cudaSuccess ||
-                cudaStreamSynchronize(st) != cudaSuccess)
-                return SW_ECUDA;
-            queue.push_back(id);
+            staged_delta.insert(staged_delta.end(), sb.delta.begin(), sb.delta.end());
+            bytes += sb.delta.size() * sizeof(uint16_t);
+            taken.push_back(id);
             incoming.pop_front();
+        }
+        if (!taken.empty()) {
+            uint16_t *up = (uint16_t *)g_words.get(bytes);
+            if (!up) return SW_ECUDA;
+            std::memcpy(up, staged_delta.data(), bytes);
+            size_t pos = 0;
+            for (int id : taken) {
+                size_t cnt = (size_t)slots[id].n * slots[id].k;
+                if (cudaMemcpyAsync(L.delta16 + slots[id].delta_off, up + pos, cnt * sizeof(uint16_t),
+                                    cudaMemcpyHostToDevice, st) != cudaSuccess)
+                    return SW_ECUDA;
+                pos += cnt;
+                queue.push_back(id);
+            }
+            staged_delta.clear();
+            if (cudaStreamSynchronize(st) != cudaSuccess) return SW_ECUDA;  // staging is reused next
         }
     }
     // n = 1 needs no search
@@ -1162,18 +1229,25 @@ int sw_server::admit_some() {
             ++it;
         }
     }
-    // admission by memory budget
+    // admission by memory budget: every waiting request whose roots and
+    // first tables keep both pools under the budget, in one call
     std::vector<int> ids;
-    while (!queue.empty()) {
-        if ((double)eng->set_pool.used > admit_frac * (double)eng->set_pool.cap ||
-            (double)eng->tab_pool.used > admit_frac * (double)eng->tab_pool.cap)
+    double sets_used = (double)eng->set_pool.used, tab_used = (double)eng->tab_pool.used;
+    for (int id : queue) {
+        const Inst &x = slots[id];
+        double s_need = x.n + 1.0, t_need = 64.0 + 4.0 * x.n + 64.0;
+        if (sets_used + s_need > admit_frac * (double)eng->set_pool.cap ||
+            tab_used + t_need > admit_frac * (double)eng->tab_pool.cap)
             break;
-        ids.assign(1, queue.front());
+        sets_used += s_need;
+        tab_used += t_need;
+        ids.push_back(id);
+    }
+    if (!ids.empty()) {
         size_t taken = 0;
         int rc = eng->admit(ids, 0, &taken);
         if (rc) return rc;
-        if (!taken) break;
-        queue.pop_front();
+        queue.erase(queue.begin(), queue.begin() + (std::ptrdiff_t)taken);
     }
     n_queued = (int32_t)queue.size();
     return SW_OK;
@@ -1500,7 +1574,8 @@ int32_t sw_batch_device(int32_t count, const int32_t *n, const int32_t *k, const
 int32_t sw_last_stats(int64_t *pairs, int64_t *candidates, int32_t *iterations, double *meet_ms,
                       double *expand_ms, double *compact_ms, int32_t *meet_launches, int64_t *launches,
                       int32_t *waves, int32_t *evictions, int64_t *arena_peak, int64_t *and_iters,
-                      int64_t *rows_transposed, double *words_ms, double *run_ms, double *sync_ms) {
+                      int64_t *rows_transposed, double *words_ms, double *run_ms, double *sync_ms,
+                      double *select_ms, double *update_ms) {
     if (pairs) *pairs = g_stats.pairs;
     if (candidates) *candidates = g_stats.candidates;
     if (iterations) *iterations = g_stats.iterations;
@@ -1517,6 +1592,8 @@ int32_t sw_last_stats(int64_t *pairs, int64_t *candidates, int32_t *iterations, 
     if (words_ms) *words_ms = g_stats.words_ms;
     if (run_ms) *run_ms = g_stats.run_ms;
     if (sync_ms) *sync_ms = g_stats.sync_ms;
+    if (select_ms) *select_ms = g_stats.select_ms;
+    if (update_ms) *update_ms = g_stats.update_ms;
     return SW_OK;
 }
 
@@ -1534,6 +1611,7 @@ void sw_set_options(const sw_options *opt) {
     if (g_opt.meet_b_tile < 0) g_opt.meet_b_tile = 0;
     if (g_opt.meet_algo != 1) g_opt.meet_algo = 0;
     if (g_opt.meet_f_rows < 0) g_opt.meet_f_rows = 0;
+    if (g_opt.meet_lane_words != 4) g_opt.meet_lane_words = 0;
 }
 
 int32_t sw_server_create(void *workspace, size_t ws_bytes, int32_t n_max, int32_t k_max, int32_t max_requests,

@@ -771,24 +771,28 @@ __global__ void __launch_bounds__(NT) k_meet(const MeetJob *__restrict__ jobs, i
 // The least meeting canonical position f is kept with atomicMin; rows at or
 // past the best f found so far are passed over.
 //
-// Shared layout: M_q occupies kBmWords(LW) 32-bit words; lane l's 2*LW
-// words (rows 64*LW*l ..) sit at unit (l ^ (q & 31)) of the row, so that
-// the AND loop's 8- or 16-byte loads are aligned and conflict-free and the
-// transposing stores are at most 2*LW-way conflicted.
+// Shared layout: M_q occupies kWords = 64*LW 32-bit words, cut into units of
+// U words (16 bytes, or 8 when LW = 1); lane l owns units l + 32h,
+// h < UPL, and unit u of state q sits at position u ^ (q & (units - 1)),
+// so that every quarter-warp's 16-byte loads in the AND loop hit distinct
+// banks and the transposing stores are at most 4-way conflicted.
 template <int LW>
 struct Bm {
-    static constexpr int kRows = 2048 * LW;  // backward sets per chunk
-    static constexpr int kWords = 64 * LW;   // 32-bit words per state bitmap
-    static constexpr int kUnit = 2 * LW;     // 32-bit words per lane
+    static constexpr int kRows = 2048 * LW;          // backward sets per chunk
+    static constexpr int kWords = 64 * LW;           // 32-bit words per state bitmap
+    static constexpr int U = LW >= 2 ? 4 : 2;        // 32-bit words per unit
+    static constexpr int UPL = 2 * LW / U;           // units per lane
+    static constexpr int kUnits = 32 * UPL;          // units per state bitmap
     __device__ static __forceinline__ int pos(int q, int g) {
-        return q * kWords + (((g / kUnit) ^ (q & 31)) * kUnit) + (g % kUnit);
+        return q * kWords + (((g / U) ^ (q & (kUnits - 1))) * U) + (g % U);
     }
+    // first row of lane l's unit h within the chunk
+    __device__ static __forceinline__ int row0(int lane, int h) { return (lane + 32 * h) * 32 * U; }
 };
 
-// Backward rows per chunk for W words per set (host and device).
+// Words per lane of the running AND by default (4 only on request).
 __host__ __device__ constexpr int bm_lanes_words(int W) { return W <= 3 ? 2 : 1; }
-__host__ __device__ constexpr int bm_rows(int W) { return 2048 * bm_lanes_words(W); }
-__host__ __device__ constexpr int bm_smem_bytes(int W) { return 64 * W * 64 * bm_lanes_words(W) * 4; }
+__host__ __device__ constexpr int bm_smem_bytes(int W, int LW) { return 64 * W * 64 * LW * 4; }
 constexpr int kBmThreads = 512;
 
 // 32x32 bit transpose across a warp: lane j holds row j on entry (bit i =
@@ -804,7 +808,7 @@ __device__ __forceinline__ uint32_t warp_transpose32(uint32_t v, int lane) {
     return v;
 }
 
-template <int W, int NT>
+template <int W, int LW, int NT>
 __global__ void __launch_bounds__(NT) k_meet_bm(const MeetJob *__restrict__ jobs, int njobs,
                                                 const int64_t *__restrict__ ntiles_p, int tf_rows,
                                                 const uint64_t *__restrict__ sets,
@@ -814,9 +818,9 @@ __global__ void __launch_bounds__(NT) k_meet_bm(const MeetJob *__restrict__ jobs
                                                 unsigned long long *and_iters,
                                                 unsigned long long *rows_transposed,
                                                 const int32_t *__restrict__ meta) {
-    constexpr int LW = bm_lanes_words(W);
     constexpr int HN = card_slots(W);
     using G = Bm<LW>;
+    constexpr int HW = G::U / 2;  // 64-bit acc words per unit
     const int64_t ntiles = *ntiles_p;
     extern __shared__ __align__(16) uint32_t sT[];  // [64 W][G::kWords]
     __shared__ int64_t s_job;
@@ -907,7 +911,7 @@ __global__ void __launch_bounds__(NT) k_meet_bm(const MeetJob *__restrict__ jobs
                 rows = (int)min((int64_t)nb, end - b0);
 #pragma unroll
                 for (int j = 0; j < LW; ++j) {
-                    int lim = rows - 64 * (LW * lane + j);
+                    int lim = rows - (G::row0(lane, j / HW) + 64 * (j % HW));
                     mask[j] = lim >= 64 ? ~0ull : (lim > 0 ? ((1ull << lim) - 1) : 0ull);
                 }
                 last_card = card;
@@ -921,17 +925,21 @@ __global__ void __launch_bounds__(NT) k_meet_bm(const MeetJob *__restrict__ jobs
                 // one AND step with the bitmap of state q; the first three
                 // steps skip the vote (a chunk almost never empties that soon)
                 auto step = [&](int q, bool vote) {
-                    const uint32_t *p = sT + q * G::kWords + ((lane ^ (q & 31)) * G::kUnit);
-                    uint64_t any;
-                    if constexpr (LW == 2) {
-                        uint4 v = *reinterpret_cast<const uint4 *>(p);
-                        acc[0] &= ((uint64_t)v.y << 32) | v.x;
-                        acc[LW - 1] &= ((uint64_t)v.w << 32) | v.z;
-                        any = acc[0] | acc[LW - 1];
-                    } else {
-                        uint2 v = *reinterpret_cast<const uint2 *>(p);
-                        acc[0] &= ((uint64_t)v.y << 32) | v.x;
-                        any = acc[0];
+                    const uint32_t *row = sT + q * G::kWords;
+                    uint64_t any = 0;
+#pragma unroll
+                    for (int h = 0; h < G::UPL; ++h) {
+                        const uint32_t *p = row + (((lane + 32 * h) ^ (q & (G::kUnits - 1))) * G::U);
+                        if constexpr (G::U == 4) {
+                            uint4 v = *reinterpret_cast<const uint4 *>(p);
+                            acc[h * HW] &= ((uint64_t)v.y << 32) | v.x;
+                            acc[h * HW + HW - 1] &= ((uint64_t)v.w << 32) | v.z;
+                            any |= acc[h * HW] | acc[h * HW + HW - 1];
+                        } else {
+                            uint2 v = *reinterpret_cast<const uint2 *>(p);
+                            acc[h] &= ((uint64_t)v.y << 32) | v.x;
+                            any |= acc[h];
+                        }
                     }
                     ++steps;
                     if (vote) alive = __any_sync(0xffffffffu, any != 0);
@@ -975,7 +983,8 @@ __global__ void __launch_bounds__(NT) k_meet_bm(const MeetJob *__restrict__ jobs
                             if (acc[t]) j = t;
                         unsigned long long key =
                             ((unsigned long long)f << 32) |
-                            (unsigned long long)(b0 + 64 * (LW * lane + j) + __ffsll((long long)acc[j]) - 1);
+                            (unsigned long long)(b0 + G::row0(lane, j / HW) + 64 * (j % HW) +
+                                                 __ffsll((long long)acc[j]) - 1);
                         atomicMin(&s_best, key);
                         atomicMin(best + J.slot, key);
                     }

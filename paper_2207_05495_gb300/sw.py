@@ -33,6 +33,7 @@ class SwError(RuntimeError):
 class sw_options(ctypes.Structure):
     _fields_ = [("meet_algo", ctypes.c_int32), ("meet_rows_per_thread", ctypes.c_int32),
                 ("meet_b_tile", ctypes.c_int32), ("meet_f_rows", ctypes.c_int32),
+                ("meet_lane_words", ctypes.c_int32),
                 ("dir_theta", ctypes.c_double), ("set_cost", ctypes.c_double)]
 
 
@@ -62,7 +63,7 @@ def lib():
         L.sw_batch.restype = i32
         L.sw_batch_device.argtypes = [i32, p, p, p, p, p, p, sz, p, p, p, i64]
         L.sw_batch_device.restype = i32
-        L.sw_last_stats.argtypes = [p] * 16
+        L.sw_last_stats.argtypes = [p] * 18
         L.sw_last_stats.restype = i32
         L.sw_set_timing.argtypes = [i32]
         L.sw_set_timing.restype = None
@@ -218,17 +219,19 @@ def sw_last_stats() -> dict:
     pairs, cand, launches, peak = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int64()
     iters, rows = ctypes.c_int64(), ctypes.c_int64()
     wms, rms, sms = ctypes.c_double(), ctypes.c_double(), ctypes.c_double()
+    sel, upd = ctypes.c_double(), ctypes.c_double()
     it, ml, wv, ev = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32()
     mm, em, cm = ctypes.c_double(), ctypes.c_double(), ctypes.c_double()
     lib().sw_last_stats(ctypes.byref(pairs), ctypes.byref(cand), ctypes.byref(it), ctypes.byref(mm),
                         ctypes.byref(em), ctypes.byref(cm), ctypes.byref(ml), ctypes.byref(launches),
                         ctypes.byref(wv), ctypes.byref(ev), ctypes.byref(peak), ctypes.byref(iters),
-                        ctypes.byref(rows), ctypes.byref(wms), ctypes.byref(rms), ctypes.byref(sms))
+                        ctypes.byref(rows), ctypes.byref(wms), ctypes.byref(rms), ctypes.byref(sms),
+                        ctypes.byref(sel), ctypes.byref(upd))
     return {"pairs": pairs.value, "candidates": cand.value, "iterations": it.value, "meet_ms": mm.value,
             "expand_ms": em.value, "compact_ms": cm.value, "meet_launches": ml.value,
             "launches": launches.value, "waves": wv.value, "evictions": ev.value, "arena_peak": peak.value,
             "and_iters": iters.value, "rows_transposed": rows.value, "words_ms": wms.value,
-            "run_ms": rms.value, "sync_ms": sms.value}
+            "run_ms": rms.value, "sync_ms": sms.value, "select_ms": sel.value, "update_ms": upd.value}
 
 
 def sw_set_timing(on: bool) -> None:

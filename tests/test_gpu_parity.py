@@ -29,12 +29,13 @@ def ws(sw):
     return sw.workspace(512 << 20)
 
 
-@pytest.fixture(params=[0, 1], ids=["bitmap", "lop3"])
+@pytest.fixture(params=[(0, 0), (0, 4), (1, 0)], ids=["bitmap", "bitmap8192", "lop3"])
 def meet_algo(sw, request):
-    """Runs a test under both meet kernels (vertical bitmaps, direct LOP3)."""
+    """Runs a test under each meet kernel: vertical bitmaps (default chunk,
+    and 8192-set chunks), and the direct LOP3 test."""
     old = sw.sw_get_options()
     o = sw.sw_get_options()
-    o.meet_algo = request.param
+    o.meet_algo, o.meet_lane_words = request.param
     sw.sw_set_options(o)
     yield request.param
     sw.sw_set_options(old)
