@@ -232,7 +232,7 @@ struct Layout {
     char *mirror;
     size_t mirror_bytes;
     uint64_t *counts;  // per-job survivors
-    int64_t *ntiles;   // meet tiles of the current iteration
+    int64_t *ntiles;   // meet tiles of the current iteration, then the bitmap kernel's tile counter
     unsigned long long *best;
     uint32_t *word_status;
     uint32_t *status;
@@ -288,7 +288,7 @@ size_t small_area_bytes(int32_t count, int64_t delta_elems, int W = 9) {
     auto add = [&](size_t x) { b += (x + 255) & ~(size_t)255; };
     add(mirror_bytes_for(count));
     add(c * sizeof(uint64_t));
-    add(sizeof(int64_t));
+    add(2 * sizeof(int64_t));
     add(c * sizeof(unsigned long long));
     add(c * sizeof(uint32_t));
     add(sizeof(uint32_t));
@@ -308,7 +308,7 @@ bool carve(void *ws, size_t bytes, int W, int32_t count, int64_t delta_elems, La
     L.mirror_bytes = mirror_bytes_for(count);
     L.mirror = cv.take<char>(L.mirror_bytes);
     L.counts = cv.take<uint64_t>(c);
-    L.ntiles = cv.take<int64_t>(1);
+    L.ntiles = cv.take<int64_t>(2);
     L.best = cv.take<unsigned long long>(c);
     L.word_status = cv.take<uint32_t>(c);
     L.status = cv.take<uint32_t>(1);
@@ -434,7 +434,7 @@ cudaError_t launch_meet_r(const MeetJob *jobs, int njobs, const int64_t *ntiles,
 }
 
 template <int W, int LW, int NT>
-cudaError_t launch_meet_bm(const MeetJob *jobs, int njobs, const int64_t *ntiles, int tf_rows, const uint64_t *sets,
+cudaError_t launch_meet_bm(const MeetJob *jobs, int njobs, int64_t *ntiles, int tf_rows, const uint64_t *sets,
                            const uint32_t *perm, const uint4 *rec, unsigned long long *best, unsigned long long *pairs, unsigned long long *iters,
                            unsigned long long *rows, const int32_t *meta, cudaStream_t st) {
     auto kern = k_meet_bm<W, LW, NT>;
@@ -514,7 +514,7 @@ struct Ops {
         g_stats.launches += 2;
         const int64_t TF = c.algo == 0 ? (int64_t)c.tf_rows : (int64_t)c.nt * c.R;
         k_meet_prep<<<1, 1024, 0, st>>>(jobs, nj, L.counts, TF, c.tb, L.ntiles);
-        const int64_t *ntiles = L.ntiles;
+        int64_t *ntiles = L.ntiles;
         if (c.algo == 0) {
             if constexpr (W <= 3)
                 if (c.lw == 4)
@@ -645,9 +645,14 @@ struct Engine {
     // Set slots of a cardinality table (int32[card_slots(W)]) kept in the set pool.
     int64_t ge_slots() const { return (card_slots(W) + 2 * W - 1) / (2 * W); }
 
+    // A level of at least this many sets gets a chunk of its own, trimmed to
+    // its survivors after compaction, instead of a chunk with room for more.
+    static constexpr int64_t kBigLevel = int64_t(1) << 22;
+
     // n contiguous set slots for instance x: from the end of its last chunk,
     // else from a new chunk (room for about three more levels of this size
-    // when the pool allows); -1 when the pool has no room.
+    // when the pool allows, or exactly n for a big level); -1 when the pool
+    // has no room.
     int64_t inst_alloc(Inst &x, int64_t n) {
         if (n < 1) n = 1;
         if (!x.chunks.empty()) {
@@ -658,7 +663,8 @@ struct Engine {
                 return off;
             }
         }
-        int64_t want = std::max<int64_t>(4 * n, x.chunks.empty() ? 8 * ((int64_t)x.n + 1) : x.chunks.back().cap * 3 / 2);
+        int64_t grow = x.chunks.empty() ? 8 * ((int64_t)x.n + 1) : std::min(x.chunks.back().cap * 3 / 2, kBigLevel);
+        int64_t want = n >= kBigLevel ? n : std::max<int64_t>(4 * n, grow);
         int64_t off = set_pool.alloc(want);
         if (off < 0) {
             want = n;
@@ -669,10 +675,16 @@ struct Engine {
         return off;
     }
 
-    // Returns the unused end of x's most recent allocation [off, off + had).
+    // Returns the unused end of x's most recent allocation [off, off + had);
+    // a big level's own chunk gives that end back to the pool.
     void inst_shrink(Inst &x, int64_t off, int64_t had, int64_t keep) {
         Chunk &c = x.chunks.back();
-        if (off + had == c.off + c.used) c.used -= had - keep;
+        if (off + had != c.off + c.used) return;
+        c.used -= had - keep;
+        if (had >= kBigLevel && c.off == off && c.cap > c.used) {
+            set_pool.release(c.off + c.used, c.cap - c.used);
+            c.cap = c.used;
+        }
     }
 
     bool stage_begin() {
@@ -799,13 +811,14 @@ struct Engine {
         std::vector<Sel> sel;
         int64_t ncand = 0;
         size_t seg_count = 0;
-        for (int id : active) {
+        // reserves candidates, table growth and the new level's slots for a
+        // step of x in direction d; false (nothing kept) when one does not fit
+        auto try_step = [&](int id, int d) -> bool {
             Inst &x = I[id];
-            int d = choose_dir(x);
             int64_t pc = x.lev[d].back().cnt;
             int64_t nc = pc * x.k;
             int64_t ncp = round_up(nc, kScanBlock);
-            if (ncand + ncp > L.cap_cand) continue;
+            if (ncand + ncp > L.cap_cand) return false;
             size_t segs_here = 0;
             int64_t nt = -1, ntc = 0;
             if (2 * (x.stored[d] + nc) > x.tab_cap[d]) {  // grow the table: load stays <= 1/2
@@ -813,9 +826,9 @@ struct Engine {
                 segs_here = x.lev[d].size();
                 if (!stg.fits((seg_count + segs_here) * sizeof(RehashSeg) + (sel.size() + 2) * sizeof(ExpandJob) +
                               (sel.size() + 1) * sizeof(FillJob)))
-                    continue;
+                    return false;
                 nt = tab_pool.alloc(ntc);
-                if (nt < 0) continue;
+                if (nt < 0) return false;
             }
             // the level's cardinality table (backward) and then the level
             // itself, last in the chunk so that its unused end can be returned
@@ -827,7 +840,7 @@ struct Engine {
             int64_t dest = inst_alloc(x, nc);
             if (dest < 0) {
                 if (nt >= 0) tab_pool.release(nt, ntc);
-                continue;
+                return false;
             }
             if (nt >= 0) {
                 tab_pool.release(x.tab_off[d], x.tab_cap[d]);
@@ -837,6 +850,13 @@ struct Engine {
             }
             sel.push_back({id, d, nc, dest, nt, ntc, ge});
             ncand += ncp;
+            return true;
+        };
+        for (int id : active) {
+            // a step that does not fit in memory counts as infinitely
+            // expensive (Section 2.1.2), so the other direction is tried
+            const int d = choose_dir(I[id]);
+            if (!try_step(id, d)) try_step(id, 1 - d);
         }
         if (sel.empty()) {
             // nothing fits: set back the instance holding the most memory

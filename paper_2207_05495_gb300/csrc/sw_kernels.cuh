@@ -48,7 +48,8 @@ struct MeetJob {
 // Lays out the meet tiles on the device once the new levels' sizes are
 // known: fills the size of the level each job just produced, its tiles
 // (tf_rows forward rows x tb backward rows; none if a level is empty) and
-// the exclusive scan of tile counts; *ntiles = their total.  One block.
+// the exclusive scan of tile counts; ntiles[0] = their total, ntiles[1] =
+// 0 (the tile counter of the bitmap meet kernel).  One block.
 __global__ void __launch_bounds__(1024) k_meet_prep(MeetJob *__restrict__ jobs, int njobs,
                                                     const uint64_t *__restrict__ counts, int64_t tf_rows,
                                                     int64_t tb, int64_t *__restrict__ ntiles) {
@@ -88,7 +89,10 @@ __global__ void __launch_bounds__(1024) k_meet_prep(MeetJob *__restrict__ jobs, 
         if (threadIdx.x == 1023) carry = before + tiles;
         __syncthreads();
     }
-    if (threadIdx.x == 0) *ntiles = carry;
+    if (threadIdx.x == 0) {
+        ntiles[0] = carry;
+        ntiles[1] = 0;  // tile counter of the bitmap meet kernel
+    }
 }
 
 // Backward levels are stored in decreasing order of cardinality (the order of
@@ -772,28 +776,28 @@ __global__ void __launch_bounds__(NT) k_meet(const MeetJob *__restrict__ jobs, i
 // past the best f found so far are passed over.
 //
 // Shared layout: M_q occupies kWords = 64*LW 32-bit words, cut into units of
-// U words (16 bytes, or 8 when LW = 1); lane l owns units l + 32h,
-// h < UPL, and unit u of state q sits at position u ^ (q & (units - 1)),
-// so that every quarter-warp's 16-byte loads in the AND loop hit distinct
-// banks and the transposing stores are at most 4-way conflicted.
+// U words (16 bytes, or 8 when LW = 1); lane l owns units l + 32h, h < UPL.
+// Consecutive bitmaps are kStride = kWords + U words apart: in the AND loop a
+// warp reads one bitmap as one contiguous run (no bank conflict), and the
+// padding of one unit per state spreads the transposing stores (one state
+// per lane, same word) over the banks, at most 4-way conflicted.
 template <int LW>
 struct Bm {
     static constexpr int kRows = 2048 * LW;          // backward sets per chunk
     static constexpr int kWords = 64 * LW;           // 32-bit words per state bitmap
     static constexpr int U = LW >= 2 ? 4 : 2;        // 32-bit words per unit
     static constexpr int UPL = 2 * LW / U;           // units per lane
-    static constexpr int kUnits = 32 * UPL;          // units per state bitmap
-    __device__ static __forceinline__ int pos(int q, int g) {
-        return q * kWords + (((g / U) ^ (q & (kUnits - 1))) * U) + (g % U);
-    }
+    static constexpr int kStride = kWords + U;       // words from one bitmap to the next
+    __host__ __device__ static constexpr int pos(int q, int g) { return q * kStride + g; }
     // first row of lane l's unit h within the chunk
     __device__ static __forceinline__ int row0(int lane, int h) { return (lane + 32 * h) * 32 * U; }
 };
 
 // Words per lane of the running AND by default (4 only on request).
 __host__ __device__ constexpr int bm_lanes_words(int W) { return W <= 3 ? 2 : 1; }
-__host__ __device__ constexpr int bm_smem_bytes(int W, int LW) { return 64 * W * 64 * LW * 4; }
+__host__ __device__ constexpr int bm_smem_bytes(int W, int LW) { return 64 * W * (64 * LW + (LW >= 2 ? 4 : 2)) * 4; }
 constexpr int kBmThreads = 512;
+static_assert(bm_smem_bytes(3, 2) == 64 * 3 * Bm<2>::kStride * 4, "bitmap layout size");
 
 // 32x32 bit transpose across a warp: lane j holds row j on entry (bit i =
 // entry (j, i)); on exit lane i holds column i (bit j = entry (j, i)).
@@ -810,7 +814,7 @@ __device__ __forceinline__ uint32_t warp_transpose32(uint32_t v, int lane) {
 
 template <int W, int LW, int NT>
 __global__ void __launch_bounds__(NT) k_meet_bm(const MeetJob *__restrict__ jobs, int njobs,
-                                                const int64_t *__restrict__ ntiles_p, int tf_rows,
+                                                int64_t *__restrict__ ntiles_p, int tf_rows,
                                                 const uint64_t *__restrict__ sets,
                                                 const uint32_t *__restrict__ perm,
                                                 const uint4 *__restrict__ rec,
@@ -821,15 +825,23 @@ __global__ void __launch_bounds__(NT) k_meet_bm(const MeetJob *__restrict__ jobs
     constexpr int HN = card_slots(W);
     using G = Bm<LW>;
     constexpr int HW = G::U / 2;  // 64-bit acc words per unit
-    const int64_t ntiles = *ntiles_p;
-    extern __shared__ __align__(16) uint32_t sT[];  // [64 W][G::kWords]
-    __shared__ int64_t s_job;
+    const int64_t ntiles = ntiles_p[0];
+    // tiles are handed out one at a time from the counter ntiles_p[1]
+    // (zeroed by k_meet_prep), in increasing order, so that a CTA that drew
+    // cheap or skipped tiles takes more of them
+    unsigned long long *next_tile = reinterpret_cast<unsigned long long *>(ntiles_p + 1);
+    extern __shared__ __align__(16) uint32_t sT[];  // [64 W][G::kStride]
+    __shared__ int64_t s_job, s_tile;
     __shared__ int s_skip;
     __shared__ unsigned long long s_best;
     constexpr int NW = NT / 32;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     unsigned long long my_pairs = 0, my_iters = 0, my_rows = 0;
-    for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+    for (;;) {
+        if (threadIdx.x == 0) s_tile = (int64_t)atomicAdd(next_tile, 1ull);
+        __syncthreads();
+        const int64_t tile = s_tile;
+        if (tile >= ntiles) break;
         if (threadIdx.x == 0) {
             int lo = 0, hi = njobs - 1;
             while (lo < hi) {
@@ -925,11 +937,11 @@ __global__ void __launch_bounds__(NT) k_meet_bm(const MeetJob *__restrict__ jobs
                 // one AND step with the bitmap of state q; the first three
                 // steps skip the vote (a chunk almost never empties that soon)
                 auto step = [&](int q, bool vote) {
-                    const uint32_t *row = sT + q * G::kWords;
+                    const uint32_t *row = sT + q * G::kStride + lane * G::U;
                     uint64_t any = 0;
 #pragma unroll
                     for (int h = 0; h < G::UPL; ++h) {
-                        const uint32_t *p = row + (((lane + 32 * h) ^ (q & (G::kUnits - 1))) * G::U);
+                        const uint32_t *p = row + 32 * h * G::U;
                         if constexpr (G::U == 4) {
                             uint4 v = *reinterpret_cast<const uint4 *>(p);
                             acc[h * HW] &= ((uint64_t)v.y << 32) | v.x;
@@ -944,12 +956,12 @@ __global__ void __launch_bounds__(NT) k_meet_bm(const MeetJob *__restrict__ jobs
                     ++steps;
                     if (vote) alive = __any_sync(0xffffffffu, any != 0);
                 };
-                const uint32_t rw[4] = {r.x, r.y, r.z, r.w};
                 const int listed = min(card, 7);
 #pragma unroll
                 for (int t = 0; t < 7; ++t) {
                     if (t >= listed || !alive) break;
-                    step((int)((rw[t >> 1] >> ((t & 1) * 16)) & 0xFFFFu), t >= 2 || t == listed - 1);
+                    const uint32_t rw = t < 2 ? r.x : t < 4 ? r.y : t < 6 ? r.z : r.w;
+                    step((int)((t & 1) ? (rw >> 16) : (rw & 0xFFFFu)), t >= 2 || t == listed - 1);
                 }
                 if (alive && card > 7) {
                     // the states after the seventh, from the set itself
@@ -977,14 +989,20 @@ __global__ void __launch_bounds__(NT) k_meet_bm(const MeetJob *__restrict__ jobs
                     for (int j = 0; j < LW; ++j) any |= acc[j];
                     unsigned ball = __ballot_sync(0xffffffffu, any != 0);
                     if (lane == __ffs(ball) - 1) {
+                        // first nonzero word of the lane, by selects (no
+                        // dynamic index, which would put acc in local memory)
                         int j = 0;
+                        uint64_t v = acc[0];
 #pragma unroll
-                        for (int t = LW - 1; t >= 0; --t)
-                            if (acc[t]) j = t;
+                        for (int t = 1; t < LW; ++t)
+                            if (v == 0) {
+                                v = acc[t];
+                                j = t;
+                            }
                         unsigned long long key =
                             ((unsigned long long)f << 32) |
                             (unsigned long long)(b0 + G::row0(lane, j / HW) + 64 * (j % HW) +
-                                                 __ffsll((long long)acc[j]) - 1);
+                                                 __ffsll((long long)v) - 1);
                         atomicMin(&s_best, key);
                         atomicMin(best + J.slot, key);
                     }

@@ -104,6 +104,23 @@ def random_automaton_ranged(n_lo: int, n_hi: int, k: int, seed: int) -> np.ndarr
             return delta
 
 
+def core_automaton(n: int, m: int, k: int, seed: int) -> np.ndarray:
+    """Every transition lands in a core C of m states scattered over Q:
+    C is a uniformly random m-subset of Q (the m smallest of n keyed draws),
+    and delta(q, a) is uniform over C for every state q, redrawn until
+    synchronizing.  After one letter every set lies inside C, so the search
+    is as deep as on an m-state automaton, while its sets (backward sets
+    above all) still spread over all ceil(n / 64) words."""
+    if not 1 <= m <= n or k < 1:
+        raise ValueError("need 1 <= m <= n and k >= 1")
+    st = _Stream(seed)
+    core = np.sort(np.argsort(st.draw(n), kind="stable")[:m])
+    while True:
+        delta = core[below(st.draw(k * n), m)].reshape(k, n).astype(np.int32)
+        if n == 1 or is_synchronizing(delta):
+            return delta
+
+
 def cerny(n: int) -> np.ndarray:
     """The Cerny automaton C_n: letter 0 (a) is the cyclic shift q -> q+1
     mod n, letter 1 (b) maps 0 to 1 and fixes every other state."""

@@ -40,3 +40,13 @@ def test_ranged_sizes():
 def test_cerny_shape():
     c = gen.cerny(5)
     assert c.tolist() == [[1, 2, 3, 4, 0], [1, 1, 2, 3, 4]]
+
+
+def test_core_automaton_lands_in_a_scattered_core():
+    d = gen.core_automaton(300, 40, 2, 1)
+    assert (d == gen.core_automaton(300, 40, 2, 1)).all() and d.shape == (2, 300)
+    core = np.unique(d)
+    assert len(core) <= 40 and core.min() >= 0 and core.max() < 300
+    # the core is spread over all five 64-bit words of a 300-state set
+    assert len(set((core // 64).tolist())) == 5
+    assert gen.is_synchronizing(d)

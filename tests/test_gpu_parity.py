@@ -2,6 +2,7 @@
 reset word and every computed level size must be identical (all integer).
 Calls go through the C-ABI (Python binding of include/sw.h)."""
 
+import functools
 import json
 import os
 
@@ -29,13 +30,15 @@ def ws(sw):
     return sw.workspace(512 << 20)
 
 
-@pytest.fixture(params=[(0, 0), (0, 4), (1, 0)], ids=["bitmap", "bitmap8192", "lop3"])
+@pytest.fixture(params=[(0, 0, 0), (0, 4, 0), (0, 0, 64), (1, 0, 0)],
+                ids=["bitmap", "bitmap8192", "bitmap_f64", "lop3"])
 def meet_algo(sw, request):
     """Runs a test under each meet kernel: vertical bitmaps (default chunk,
-    and 8192-set chunks), and the direct LOP3 test."""
+    8192-set chunks, and forward tiles of 64 rows so that a level spans many
+    tiles), and the direct LOP3 test."""
     old = sw.sw_get_options()
     o = sw.sw_get_options()
-    o.meet_algo, o.meet_lane_words = request.param
+    o.meet_algo, o.meet_lane_words, o.meet_f_rows = request.param
     sw.sw_set_options(o)
     yield request.param
     sw.sw_set_options(old)
@@ -105,6 +108,33 @@ def test_random_vs_oracle(sw, ws, meet_algo, n, k, seed):
     r, w = sw.sw_reset_threshold(h, ws=ws)
     ro, wo, fo, bo = oracle.bidir(d)
     assert (r, w) == (ro, wo)
+    assert resets(d, w)
+    fs, bs = sw.sw_level_sizes(h)
+    check_sizes(d, fs, bs)
+
+
+# Automata whose transitions all land in a scattered core of m states
+# (gen.core_automaton): oracle-sized searches whose sets, the backward ones
+# above all, spread over W = 4 .. 9 words, with levels of a few thousand sets
+# (several 2048-set backward chunks).
+CORE_CASES = [(250, 64, 3, 4), (300, 96, 2, 2), (330, 80, 2, 7), (420, 88, 2, 8), (450, 90, 2, 5),
+              (520, 72, 2, 6), (576, 80, 2, 3)]
+
+
+@functools.lru_cache(maxsize=None)
+def _core_oracle(n, m, k, seed):
+    d = gen.core_automaton(n, m, k, seed)
+    r, w, _, _ = oracle.bidir(d)
+    return r, tuple(w)
+
+
+@pytest.mark.parametrize("n,m,k,seed", CORE_CASES)
+def test_wide_sets_vs_oracle(sw, ws, meet_algo, n, m, k, seed):
+    d = gen.core_automaton(n, m, k, seed)
+    h = sw.load(d)
+    r, w = sw.sw_reset_threshold(h, ws=ws)
+    ro, wo = _core_oracle(n, m, k, seed)
+    assert (r, tuple(w)) == (ro, wo)
     assert resets(d, w)
     fs, bs = sw.sw_level_sizes(h)
     check_sizes(d, fs, bs)
