@@ -76,6 +76,10 @@ def workload(name: str, rank: int = 0):
                                                   "instances": 1}
     if name == "cerny":
         return [gen.cerny(n) for n in range(16, 29)], {"workload": "Cerny automata n=16..28", "instances": 13}
+    if name == "hard300":
+        return [gen.random_automaton(300, 2, 0)], {
+            "workload": "hard single instance: random binary automaton n=300 k=2 seed 0, 5x64-bit bitsets",
+            "instances": 1}
     raise SystemExit(f"unknown workload {name}")
 
 
@@ -266,7 +270,7 @@ def main():
     ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="c3", choices=["c3", "c1", "cerny"])
+    ap.add_argument("--workload", default="c3", choices=["c3", "c1", "cerny", "hard300"])
     ap.add_argument("--ws-gb", type=float, default=160.0)
     ap.add_argument("--cpu-budget", type=float, default=20.0)
     ap.add_argument("--one-sample", type=int, default=256)

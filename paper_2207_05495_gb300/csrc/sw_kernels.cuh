@@ -11,6 +11,7 @@
 #pragma once
 
 #include <cstdint>
+#include <type_traits>
 #include <cuda_runtime.h>
 
 namespace sw {
@@ -933,9 +934,10 @@ __global__ void __launch_bounds__(NT) k_meet_bm(const MeetJob *__restrict__ jobs
 #pragma unroll
                 for (int j = 0; j < LW; ++j) acc[j] = mask[j];
                 bool alive = true;
-                uint32_t steps = 0;
                 // one AND step with the bitmap of state q; the first three
-                // steps skip the vote (a chunk almost never empties that soon)
+                // steps skip the vote (a chunk almost never empties that
+                // soon; a row whose states run out before the third step is
+                // settled by the ballot after the walk)
                 auto step = [&](int q, bool vote) {
                     const uint32_t *row = sT + q * G::kStride + lane * G::U;
                     uint64_t any = 0;
@@ -953,16 +955,29 @@ __global__ void __launch_bounds__(NT) k_meet_bm(const MeetJob *__restrict__ jobs
                             any |= acc[h];
                         }
                     }
-                    ++steps;
                     if (vote) alive = __any_sync(0xffffffffu, any != 0);
                 };
+                // the listed states (at most seven) from the record; a row
+                // with all seven listed takes a copy of the walk without the
+                // per-step bound check.  `walked` = steps taken.
                 const int listed = min(card, 7);
+                int walked = listed;
+                auto walk = [&](auto all_listed) {
+                    constexpr bool kAll = decltype(all_listed)::value;
 #pragma unroll
-                for (int t = 0; t < 7; ++t) {
-                    if (t >= listed || !alive) break;
-                    const uint32_t rw = t < 2 ? r.x : t < 4 ? r.y : t < 6 ? r.z : r.w;
-                    step((int)((t & 1) ? (rw >> 16) : (rw & 0xFFFFu)), t >= 2 || t == listed - 1);
-                }
+                    for (int t = 0; t < 7; ++t) {
+                        if (!kAll && t >= listed) return;
+                        if (t >= 3 && !alive) {  // alive changes only at voted steps
+                            walked = t;
+                            return;
+                        }
+                        const uint32_t rw = t < 2 ? r.x : t < 4 ? r.y : t < 6 ? r.z : r.w;
+                        step((int)((t & 1) ? (rw >> 16) : (rw & 0xFFFFu)), t >= 2);
+                    }
+                };
+                if (listed == 7) walk(std::true_type{});
+                else walk(std::false_type{});
+                uint32_t steps = (uint32_t)walked;
                 if (alive && card > 7) {
                     // the states after the seventh, from the set itself
                     const int s6 = (int)(r.w & 0xFFFFu);
@@ -978,6 +993,7 @@ __global__ void __launch_bounds__(NT) k_meet_bm(const MeetJob *__restrict__ jobs
                             const int q = lo + __ffs(bits) - 1;
                             bits &= bits - 1;
                             step(q, true);
+                            ++steps;
                         }
                     }
                 }
