@@ -934,45 +934,70 @@ __global__ void __launch_bounds__(NT) k_meet_bm(const MeetJob *__restrict__ jobs
 #pragma unroll
                 for (int j = 0; j < LW; ++j) acc[j] = mask[j];
                 bool alive = true;
-                // one AND step with the bitmap of state q; the first three
-                // steps skip the vote (a chunk almost never empties that
-                // soon; a row whose states run out before the third step is
-                // settled by the ballot after the walk)
-                auto step = [&](int q, bool vote) {
+                // An AND step with the bitmap of state q: load the lane's
+                // 2*LW words of it (load_frag), AND them into the running
+                // intersection and, from the third step on, vote (apply).
+                // The first three steps skip the vote (a chunk almost never
+                // empties that soon; a row whose states run out before the
+                // third step is settled by the ballot after the walk).
+                struct Frag {
+                    uint32_t w[2 * LW];
+                };
+                auto load_frag = [&](int q) {
+                    Frag fr;
                     const uint32_t *row = sT + q * G::kStride + lane * G::U;
-                    uint64_t any = 0;
 #pragma unroll
                     for (int h = 0; h < G::UPL; ++h) {
                         const uint32_t *p = row + 32 * h * G::U;
                         if constexpr (G::U == 4) {
-                            uint4 v = *reinterpret_cast<const uint4 *>(p);
-                            acc[h * HW] &= ((uint64_t)v.y << 32) | v.x;
-                            acc[h * HW + HW - 1] &= ((uint64_t)v.w << 32) | v.z;
-                            any |= acc[h * HW] | acc[h * HW + HW - 1];
+                            const uint4 v = *reinterpret_cast<const uint4 *>(p);
+                            fr.w[4 * h] = v.x;
+                            fr.w[4 * h + 1] = v.y;
+                            fr.w[4 * h + 2] = v.z;
+                            fr.w[4 * h + 3] = v.w;
                         } else {
-                            uint2 v = *reinterpret_cast<const uint2 *>(p);
-                            acc[h] &= ((uint64_t)v.y << 32) | v.x;
-                            any |= acc[h];
+                            const uint2 v = *reinterpret_cast<const uint2 *>(p);
+                            fr.w[2 * h] = v.x;
+                            fr.w[2 * h + 1] = v.y;
                         }
+                    }
+                    return fr;
+                };
+                auto apply = [&](const Frag &fr, bool vote) {
+                    uint64_t any = 0;
+#pragma unroll
+                    for (int j = 0; j < LW; ++j) {
+                        acc[j] &= ((uint64_t)fr.w[2 * j + 1] << 32) | fr.w[2 * j];
+                        any |= acc[j];
                     }
                     if (vote) alive = __any_sync(0xffffffffu, any != 0);
                 };
-                // the listed states (at most seven) from the record; a row
-                // with all seven listed takes a copy of the walk without the
-                // per-step bound check.  `walked` = steps taken.
-                const int listed = min(card, 7);
+                // state t (< 7) of the record
+                auto listed_state = [&](int t) -> int {
+                    const uint32_t rw = t < 2 ? r.x : t < 4 ? r.y : t < 6 ? r.z : r.w;
+                    return (int)((t & 1) ? (rw >> 16) : (rw & 0xFFFFu));
+                };
+                // The listed states (at most seven), software-pipelined: the
+                // bitmap of step t+1 is loaded before step t's AND and vote.
+                // A row with all seven listed takes a copy of the walk without
+                // the per-step bound check.  `walked` = steps taken.
+                const int listed = min(card, 7);  // >= 1: forward sets are nonempty
                 int walked = listed;
                 auto walk = [&](auto all_listed) {
                     constexpr bool kAll = decltype(all_listed)::value;
+                    Frag cur = load_frag(listed_state(0));
 #pragma unroll
                     for (int t = 0; t < 7; ++t) {
-                        if (!kAll && t >= listed) return;
-                        if (t >= 3 && !alive) {  // alive changes only at voted steps
-                            walked = t;
+                        const bool more = kAll ? (t < 6) : (t + 1 < listed);
+                        Frag nxt;
+                        if (more) nxt = load_frag(listed_state(t + 1 < 7 ? t + 1 : 6));
+                        apply(cur, t >= 2);
+                        if (!more) return;
+                        if (t >= 2 && !alive) {
+                            walked = t + 1;
                             return;
                         }
-                        const uint32_t rw = t < 2 ? r.x : t < 4 ? r.y : t < 6 ? r.z : r.w;
-                        step((int)((t & 1) ? (rw >> 16) : (rw & 0xFFFFu)), t >= 2);
+                        cur = nxt;
                     }
                 };
                 if (listed == 7) walk(std::true_type{});
@@ -992,7 +1017,7 @@ __global__ void __launch_bounds__(NT) k_meet_bm(const MeetJob *__restrict__ jobs
                         while (bits && alive) {
                             const int q = lo + __ffs(bits) - 1;
                             bits &= bits - 1;
-                            step(q, true);
+                            apply(load_frag(q), true);
                             ++steps;
                         }
                     }
