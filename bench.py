@@ -48,6 +48,13 @@ INT32_LANES_PER_SM = 128
 SMEM_BYTES_PER_CLK_SM = 128
 SM_MAX_MHZ_FALLBACK = 2070.0
 N_SMS_NOMINAL = 152
+# DRAM bytes (read + write) of the meet kernel per backward row it
+# transposes, from an ncu capture (dram__bytes_read.sum +
+# dram__bytes_write.sum) of every meet launch of two steps of the first 512
+# automata of this workload; the full workload is too large for a
+# multi-pass capture, so its traffic per launch is this figure times the
+# rows one launch transposes.
+MEET_DRAM_BYTES_PER_ROW = 14.2
 
 
 def rank_seeds(rank: int, count: int) -> range:
@@ -445,7 +452,10 @@ def main():
         "e2e": {"value": count * world / e2e_s, "unit": "instances/s", "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h},
         "roofline": {"bound": "alu", "kernel": "k_meet_bm", "achieved": achieved, "peak": peak, "unit": "Tops/s",
-                     "frac": achieved / peak if peak else None, "traffic": None,
+                     "frac": achieved / peak if peak else None,
+                     "traffic": MEET_DRAM_BYTES_PER_ROW * rows_t / max(launches, 1) if args.workload == "c3" else None,
+                     "traffic_basis": "ncu dram__bytes_read.sum + dram__bytes_write.sum per transposed backward row, "
+                                      "measured on the first 512 automata of this workload, times rows per launch",
                      "work": "int32 ops executed: 64 per 64-bit lane word per warp AND step + 25 per transposed 32-bit row word",
                      "and_steps_per_step": iters, "rows_transposed_per_step": rows_t,
                      "smem_tbs": smem_bytes / sec / 1e12 if sec > 0 else 0.0, "smem_peak_tbs": smem_peak,

@@ -1,10 +1,10 @@
 """Autotuner for the search's tunable parameters (sw_options).
 
 It times the batched search on a sample of automata for every candidate
-setting of the meet kernel's forward rows per tile and of the direction
-rule (SetCost and the threshold theta of the step-cost comparison,
-Section 2.1.2), requires every candidate to return identical r and words,
-and keeps the fastest.  Results are cached in tuned.json next to this file,
+setting of the meet kernel's forward rows per tile and backward chunk size
+(lane words), and of the direction rule (SetCost and the threshold theta of
+the step-cost comparison, Section 2.1.2), requires every candidate to
+return identical r and words, and keeps the fastest.  Results are cached in tuned.json next to this file,
 keyed by (words per set W, letters k, GPU name); `apply` loads the entry for
 a workload into the calling thread's options.
 
@@ -26,7 +26,8 @@ CACHE = os.path.join(os.path.dirname(os.path.abspath(__file__)), "tuned.json")
 
 GRID = {
     "meet_f_rows": [1024, 4096, 16384],
-    "set_cost": [2048.0, 8192.0, 32768.0],
+    "meet_lane_words": [0, 4],
+    "set_cost": [8192.0, 32768.0, 131072.0],
     "dir_theta": [0.5, 1.0, 2.0],
 }
 

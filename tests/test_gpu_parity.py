@@ -140,6 +140,37 @@ def test_wide_sets_vs_oracle(sw, ws, meet_algo, n, m, k, seed):
     check_sizes(d, fs, bs)
 
 
+def test_max_letters(sw, ws, meet_algo):
+    # k = 255 (the largest alphabet): letter ids up to 254 in the word and
+    # candidate ids p*k + a far from powers of two
+    for n, seed in ((8, 1), (12, 2)):
+        d = gen.random_automaton(n, sw.SW_MAX_LETTERS, seed)
+        h = sw.load(d)
+        r, w = sw.sw_reset_threshold(h, ws=ws)
+        ro, wo, _, _ = oracle.bidir(d)
+        assert (r, w) == (ro, wo)
+        fs, bs = sw.sw_level_sizes(h)
+        check_sizes(d, fs, bs)
+
+
+def test_ragged_batch_mixed_sizes_and_alphabets(sw, ws):
+    # one batch mixing n = 1 .. 130 (one to three words per set) and
+    # k = 1 .. 5; every instance must equal its own oracle result
+    rng = np.random.default_rng(5)
+    ds = [gen.random_automaton(1, 3, 1), gen.random_automaton(4, 1, 2), gen.random_automaton(6, 1, 3)]
+    while len(ds) < 40:
+        k = int(rng.integers(2, 6))
+        n = int(rng.integers(2, 131 if k == 2 else (90 if k == 3 else 60)))
+        ds.append(gen.random_automaton(n, k, 900 + len(ds)))
+    hs = [sw.load(d) for d in ds]
+    rb, wb = sw.sw_batch(hs, ws=ws)
+    for i, d in enumerate(ds):
+        ro, wo, _, _ = oracle.bidir(d)
+        assert (int(rb[i]), wb[i]) == (ro, wo), i
+        fs, bs = sw.sw_level_sizes(hs[i])
+        check_sizes(d, fs, bs)
+
+
 def test_batch_equals_single(sw, ws):
     ds = [gen.random_automaton(int(n), 2, 300 + i) for i, n in enumerate([5, 17, 33, 64, 65, 40, 2, 1, 90, 128])]
     hs = [sw.load(d) for d in ds]
