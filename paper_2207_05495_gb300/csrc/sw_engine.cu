@@ -392,9 +392,22 @@ struct MeetCfg {
     int lw;       // bitmap test: 64-bit words of the running AND per lane
     int R, tb, nt;
     int tf_rows;  // forward rows per tile (bitmap kernel)
+    int n_cap;    // bitmap test: state bitmaps held (no automaton of the run has more states)
 };
 
-MeetCfg meet_cfg(int W) {
+// Opt-in shared memory per block, bytes.
+int max_smem_optin() {
+    static int v = 0;
+    if (!v) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&v, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+        if (v <= 0) v = 48 * 1024;
+    }
+    return v;
+}
+
+MeetCfg meet_cfg(int W, int n_max) {
     MeetCfg c;
     int R = g_opt.meet_rows_per_thread;
     if (R != 1 && R != 2 && R != 4 && R != 8) R = default_rows(W);
@@ -407,7 +420,11 @@ MeetCfg meet_cfg(int W) {
     c.tb = std::min(tb, max_tb);
     c.nt = 256;
     c.algo = g_opt.meet_algo == 1 ? 1 : 0;
+    c.n_cap = std::max(1, std::min(64 * W, n_max));
     c.lw = g_opt.meet_lane_words == 4 && W <= 3 ? 4 : bm_lanes_words(W);
+    // wider sets: 4096-set chunks (1024 threads, one CTA per SM) whenever the
+    // bitmaps of the states that occur fit in shared memory
+    if (W >= 4 && W <= 7 && bm_smem_bytes_n(c.n_cap, 2) + 1024 <= max_smem_optin()) c.lw = 2;
     if (c.algo == 0) c.tb = 2048 * c.lw;
     c.tf_rows = g_opt.meet_f_rows > 0 ? g_opt.meet_f_rows : 4096;
     c.tf_rows = std::max(8, std::min(c.tf_rows, 1 << 20));
@@ -434,22 +451,22 @@ cudaError_t launch_meet_r(const MeetJob *jobs, int njobs, const int64_t *ntiles,
 }
 
 template <int W, int LW, int NT>
-cudaError_t launch_meet_bm(const MeetJob *jobs, int njobs, int64_t *ntiles, int tf_rows, const uint64_t *sets,
+cudaError_t launch_meet_bm(const MeetJob *jobs, int njobs, int64_t *ntiles, int tf_rows, int n_cap, const uint64_t *sets,
                            const uint32_t *perm, const uint4 *rec, unsigned long long *best, unsigned long long *pairs, unsigned long long *iters,
                            unsigned long long *rows, const int32_t *meta, cudaStream_t st) {
     auto kern = k_meet_bm<W, LW, NT>;
-    size_t smem = (size_t)bm_smem_bytes(W, LW);
-    static thread_local bool configured = false;
-    if (!configured) {
+    size_t smem = (size_t)bm_smem_bytes_n(n_cap, LW);
+    static thread_local size_t configured = 0;
+    if (configured < smem) {
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
-        configured = true;
+        configured = smem;
     }
     int per_sm = 0;
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, NT, smem);
     int64_t grid = (int64_t)sm_count() * std::max(per_sm, 1);
-    kern<<<(unsigned)grid, NT, smem, st>>>(jobs, njobs, ntiles, tf_rows, sets, perm, rec, best, pairs, iters, rows,
-                                           meta);
+    kern<<<(unsigned)grid, NT, smem, st>>>(jobs, njobs, ntiles, tf_rows, n_cap, sets, perm, rec, best, pairs, iters,
+                                           rows, meta);
     return cudaGetLastError();
 }
 
@@ -518,10 +535,14 @@ struct Ops {
         if (c.algo == 0) {
             if constexpr (W <= 3)
                 if (c.lw == 4)
-                    return launch_meet_bm<W, 4, 1024>(jobs, nj, ntiles, c.tf_rows, L.sets, L.perm, L.rec, L.best,
-                                                      L.pairs, L.pairs + 1, L.pairs + 2, L.meta, st);
-            return launch_meet_bm<W, bm_lanes_words(W), kBmThreads>(jobs, nj, ntiles, c.tf_rows, L.sets, L.perm,
-                                                                    L.rec, L.best, L.pairs, L.pairs + 1,
+                    return launch_meet_bm<W, 4, 1024>(jobs, nj, ntiles, c.tf_rows, c.n_cap, L.sets, L.perm, L.rec,
+                                                      L.best, L.pairs, L.pairs + 1, L.pairs + 2, L.meta, st);
+            if constexpr (W >= 4 && W <= 7)
+                if (c.lw == 2)
+                    return launch_meet_bm<W, 2, 1024>(jobs, nj, ntiles, c.tf_rows, c.n_cap, L.sets, L.perm, L.rec,
+                                                      L.best, L.pairs, L.pairs + 1, L.pairs + 2, L.meta, st);
+            return launch_meet_bm<W, bm_lanes_words(W), kBmThreads>(jobs, nj, ntiles, c.tf_rows, c.n_cap, L.sets,
+                                                                    L.perm, L.rec, L.best, L.pairs, L.pairs + 1,
                                                                     L.pairs + 2, L.meta, st);
         }
         switch (c.R) {
@@ -635,9 +656,11 @@ struct Engine {
     Staging stg;
     std::vector<int> active, deferred;
 
-    Engine(int W_, cudaStream_t s, std::vector<Inst> &insts, const Layout &lay) : W(W_), st(s), L(lay), I(insts) {
+    // n_max: no instance the engine will run has more states
+    Engine(int W_, int n_max, cudaStream_t s, std::vector<Inst> &insts, const Layout &lay)
+        : W(W_), st(s), L(lay), I(insts) {
         ops = ops_for(W);
-        mc = meet_cfg(W);
+        mc = meet_cfg(W, n_max);
         set_pool.init(L.cap_sets);
         tab_pool.init(L.cap_table);
     }
@@ -1460,7 +1483,9 @@ static int32_t run_instances(std::vector<Inst> &I, const std::vector<uint16_t> *
         if (*bad) return SW_EINVAL;
     }
     if (cudaMemsetAsync(L.status, 0, sizeof(uint32_t), st) != cudaSuccess) return SW_ECUDA;
-    Engine E(W, st, I, L);
+    int n_max = 1;
+    for (auto &x : I) n_max = std::max(n_max, (int)x.n);
+    Engine E(W, n_max, st, I, L);
     E.device_words = device_words;
     E.out_words = out_words;
     auto t0 = std::chrono::steady_clock::now();
@@ -1660,7 +1685,7 @@ int32_t sw_server_create(void *workspace, size_t ws_bytes, int32_t n_max, int32_
     s->words.assign((size_t)max_requests * word_cap, 0);
     for (int i = max_requests - 1; i >= 0; --i) s->free_slots.push_back(i);
     s->delta_pool.init(s->L.delta_cap);
-    s->eng.reset(new Engine(s->W, s->st, s->slots, s->L));
+    s->eng.reset(new Engine(s->W, s->n_max, s->st, s->slots, s->L));
     s->eng->device_words = false;
     s->eng->out_words = s->words.data();
     sw_server *raw = s.get();

@@ -796,7 +796,8 @@ struct Bm {
 
 // Words per lane of the running AND by default (4 only on request).
 __host__ __device__ constexpr int bm_lanes_words(int W) { return W <= 3 ? 2 : 1; }
-__host__ __device__ constexpr int bm_smem_bytes(int W, int LW) { return 64 * W * (64 * LW + (LW >= 2 ? 4 : 2)) * 4; }
+__host__ __device__ constexpr int bm_smem_bytes_n(int n_cap, int LW) { return n_cap * (64 * LW + (LW >= 2 ? 4 : 2)) * 4; }
+__host__ __device__ constexpr int bm_smem_bytes(int W, int LW) { return bm_smem_bytes_n(64 * W, LW); }
 constexpr int kBmThreads = 512;
 static_assert(bm_smem_bytes(3, 2) == 64 * 3 * Bm<2>::kStride * 4, "bitmap layout size");
 
@@ -815,7 +816,7 @@ __device__ __forceinline__ uint32_t warp_transpose32(uint32_t v, int lane) {
 
 template <int W, int LW, int NT>
 __global__ void __launch_bounds__(NT) k_meet_bm(const MeetJob *__restrict__ jobs, int njobs,
-                                                int64_t *__restrict__ ntiles_p, int tf_rows,
+                                                int64_t *__restrict__ ntiles_p, int tf_rows, int n_cap,
                                                 const uint64_t *__restrict__ sets,
                                                 const uint32_t *__restrict__ perm,
                                                 const uint4 *__restrict__ rec,
@@ -831,7 +832,7 @@ __global__ void __launch_bounds__(NT) k_meet_bm(const MeetJob *__restrict__ jobs
     // (zeroed by k_meet_prep), in increasing order, so that a CTA that drew
     // cheap or skipped tiles takes more of them
     unsigned long long *next_tile = reinterpret_cast<unsigned long long *>(ntiles_p + 1);
-    extern __shared__ __align__(16) uint32_t sT[];  // [64 W][G::kStride]
+    extern __shared__ __align__(16) uint32_t sT[];  // [n_cap][G::kStride]
     __shared__ int64_t s_job, s_tile;
     __shared__ int s_skip;
     __shared__ unsigned long long s_best;
@@ -887,9 +888,10 @@ __global__ void __launch_bounds__(NT) k_meet_bm(const MeetJob *__restrict__ jobs
             }
 #pragma unroll
             for (int h = 0; h < 2 * W; ++h) {
+                if (32 * h >= n_cap) break;  // no set holds these states: no bitmap is kept
                 uint32_t v = (h & 1) ? (uint32_t)(y[h >> 1] >> 32) : (uint32_t)y[h >> 1];
                 uint32_t c = warp_transpose32(v, lane);  // column lane: state 32h + lane
-                sT[G::pos(32 * h + lane, g)] = c;
+                if (32 * h + lane < n_cap) sT[G::pos(32 * h + lane, g)] = c;
             }
         }
         __syncthreads();
