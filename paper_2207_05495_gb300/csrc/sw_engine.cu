@@ -673,7 +673,7 @@ struct Engine {
     static constexpr int64_t kBigLevel = int64_t(1) << 22;
 
     // n contiguous set slots for instance x: from the end of its last chunk,
-    // else from a new chunk (room for about three more levels of this size
+    // else from a new chunk (at least four times n and twice the last chunk
     // when the pool allows, or exactly n for a big level); -1 when the pool
     // has no room.
     int64_t inst_alloc(Inst &x, int64_t n) {
@@ -686,7 +686,7 @@ struct Engine {
                 return off;
             }
         }
-        int64_t grow = x.chunks.empty() ? 8 * ((int64_t)x.n + 1) : std::min(x.chunks.back().cap * 3 / 2, kBigLevel);
+        int64_t grow = x.chunks.empty() ? 8 * ((int64_t)x.n + 1) : std::min(x.chunks.back().cap * 2, kBigLevel);
         int64_t want = n >= kBigLevel ? n : std::max<int64_t>(4 * n, grow);
         int64_t off = set_pool.alloc(want);
         if (off < 0) {
@@ -822,20 +822,35 @@ struct Engine {
         return SW_OK;
     }
 
-    // One iteration over the active instances.
-    int iterate() {
-        g_stats.iterations++;
-        auto t_sel = std::chrono::steady_clock::now();
-        if (!stage_begin()) return SW_ECUDA;
-        struct Sel {
-            int id, d;
-            int64_t nc, dest, new_tab, new_cap, ge;
-        };
-        std::vector<Sel> sel;
+    // A planned step: instance id expands direction d into nc candidates;
+    // its new level goes to dest (set pool), ge = its cardinality table
+    // (backward) or -1, and new_tab/new_cap = the grown hash table or -1.
+    struct Sel {
+        int id, d;
+        int64_t nc, dest, new_tab, new_cap, ge;
+    };
+    std::vector<Sel> pending;    // steps planned for the next iteration
+    std::vector<char> planned;   // per instance: has a step in `pending`
+    cudaEvent_t ev_counts = nullptr;
+
+    ~Engine() {
+        if (ev_counts) cudaEventDestroy(ev_counts);
+    }
+
+    // Plans the next step of every active instance that has none in `sel`
+    // yet: chooses its direction and reserves candidates, table growth and
+    // the new level's slots.  An instance whose step does not fit either way
+    // is left out (it waits for an iteration).
+    void plan(std::vector<Sel> &sel) {
+        if (planned.size() < I.size()) planned.resize(I.size(), 0);
         int64_t ncand = 0;
         size_t seg_count = 0;
-        // reserves candidates, table growth and the new level's slots for a
-        // step of x in direction d; false (nothing kept) when one does not fit
+        for (const Sel &s : sel) {
+            ncand += round_up(s.nc, kScanBlock);
+            if (s.new_tab >= 0) seg_count += I[s.id].lev[s.d].size();
+        }
+        // staging bytes of the job arrays, checked before a table grows
+        auto staging_fits = [&](size_t bytes) { return bytes + 256 * 8 <= L.mirror_bytes; };
         auto try_step = [&](int id, int d) -> bool {
             Inst &x = I[id];
             int64_t pc = x.lev[d].back().cnt;
@@ -845,12 +860,21 @@ struct Engine {
             size_t segs_here = 0;
             int64_t nt = -1, ntc = 0;
             if (2 * (x.stored[d] + nc) > x.tab_cap[d]) {  // grow the table: load stays <= 1/2
-                ntc = round_up(3 * (x.stored[d] + nc), 64);
+                // to a load of 1/6 while small and the pool has room (fewer
+                // rehashes, shorter probes), else to a load of 1/3
+                const int64_t need = x.stored[d] + nc;
                 segs_here = x.lev[d].size();
-                if (!stg.fits((seg_count + segs_here) * sizeof(RehashSeg) + (sel.size() + 2) * sizeof(ExpandJob) +
-                              (sel.size() + 1) * sizeof(FillJob)))
+                if (!staging_fits((seg_count + segs_here) * sizeof(RehashSeg) + (sel.size() + 2) * sizeof(ExpandJob) +
+                                  (sel.size() + 1) * (sizeof(FillJob) + sizeof(MeetJob))))
                     return false;
-                nt = tab_pool.alloc(ntc);
+                if (need < (int64_t(1) << 22)) {
+                    ntc = round_up(6 * need, 64);
+                    nt = tab_pool.alloc(ntc);
+                }
+                if (nt < 0) {
+                    ntc = round_up(3 * need, 64);
+                    nt = tab_pool.alloc(ntc);
+                }
                 if (nt < 0) return false;
             }
             // the level's cardinality table (backward) and then the level
@@ -872,15 +896,29 @@ struct Engine {
                 seg_count += segs_here;
             }
             sel.push_back({id, d, nc, dest, nt, ntc, ge});
+            planned[id] = 1;
             ncand += ncp;
             return true;
         };
         for (int id : active) {
+            if (planned[id] || I[id].state != kActive) continue;
             // a step that does not fit in memory counts as infinitely
             // expensive (Section 2.1.2), so the other direction is tried
             const int d = choose_dir(I[id]);
             if (!try_step(id, d)) try_step(id, 1 - d);
         }
+    }
+
+    // One iteration over the active instances.  The next iteration's steps
+    // are planned on the host while this iteration's meet kernel runs.
+    int iterate() {
+        g_stats.iterations++;
+        auto t_sel = std::chrono::steady_clock::now();
+        if (!ev_counts) CK(cudaEventCreateWithFlags(&ev_counts, cudaEventDisableTiming));
+        std::vector<Sel> sel;
+        sel.swap(pending);
+        plan(sel);  // instances without a planned step: new, or skipped for room
+        for (const Sel &s : sel) planned[s.id] = 0;
         if (sel.empty()) {
             // nothing fits: set back the instance holding the most memory
             auto it = std::max_element(active.begin(), active.end(),
@@ -899,10 +937,12 @@ struct Engine {
             }
             return SW_OK;
         }
+        if (!stage_begin()) return SW_ECUDA;
         // jobs, table fills and rehash segments: one upload
         int nj = (int)sel.size();
         ExpandJob *d_jobs;
         ExpandJob *jobs = stg.take<ExpandJob>(nj, &d_jobs);
+        if (!stg.ok) return SW_EINTERNAL;
         std::vector<FillJob> fills;
         std::vector<RehashSeg> segs;
         int64_t cand = 0, rehash_total = 0, maxfill = 1;
@@ -933,6 +973,7 @@ struct Engine {
                 }
             }
         }
+        const int64_t ncand = cand;
         FillJob *d_fill = nullptr;
         RehashSeg *d_segs = nullptr;
         if (!fills.empty()) {
@@ -976,34 +1017,36 @@ struct Engine {
         if (g_timing) CK(cudaEventRecord(g_ev.ev[1], st));
         CK(ops.compact(d_jobs, nj, ncand, L, st));
         if (g_timing) CK(cudaEventRecord(g_ev.ev[2], st));
+        // the new levels' sizes and the status come back before the meet
+        uint64_t *down = (uint64_t *)g_down.get((2 * nj + 5) * sizeof(uint64_t));
+        if (!down) return SW_ECUDA;
+        uint64_t *d_status = down + nj, *d_best = down + nj + 1, *d_pairs = down + 2 * nj + 1;
+        CK(cudaMemcpyAsync(down, L.counts, nj * sizeof(uint64_t), cudaMemcpyDeviceToHost, st));
+        CK(cudaMemcpyAsync(d_status, L.status, sizeof(uint32_t), cudaMemcpyDeviceToHost, st));
+        CK(cudaEventRecord(ev_counts, st));
         CK(cudaMemsetAsync(L.best, 0xFF, nj * sizeof(unsigned long long), st));
         CK(cudaMemsetAsync(L.pairs, 0, 3 * sizeof(unsigned long long), st));
         if (g_timing) CK(cudaEventRecord(g_ev.ev[3], st));
         CK(ops.meet(d_mj, nj, mc, L, st));
         if (g_timing) CK(cudaEventRecord(g_ev.ev[4], st));
         g_stats.meet_launches++;
-        // one copy back: counts, status, meet results, counters
-        uint64_t *down = (uint64_t *)g_down.get((2 * nj + 5) * sizeof(uint64_t));
-        if (!down) return SW_ECUDA;
-        uint64_t *d_status = down + nj, *d_best = down + nj + 1, *d_pairs = down + 2 * nj + 1;
-        CK(cudaMemcpyAsync(down, L.counts, nj * sizeof(uint64_t), cudaMemcpyDeviceToHost, st));
-        CK(cudaMemcpyAsync(d_status, L.status, sizeof(uint32_t), cudaMemcpyDeviceToHost, st));
         CK(cudaMemcpyAsync(d_best, L.best, nj * sizeof(unsigned long long), cudaMemcpyDeviceToHost, st));
         CK(cudaMemcpyAsync(d_pairs, L.pairs, 3 * sizeof(unsigned long long), cudaMemcpyDeviceToHost, st));
-        CK(wait_stream(st));
-        if (g_timing) {
-            g_stats.expand_ms += elapsed(g_ev.ev[0], g_ev.ev[1]);
-            g_stats.compact_ms += elapsed(g_ev.ev[1], g_ev.ev[2]);
-            g_stats.meet_ms += elapsed(g_ev.ev[3], g_ev.ev[4]);
+        {
+            auto t0 = std::chrono::steady_clock::now();
+            cudaError_t e = cudaEventSynchronize(ev_counts);
+            g_stats.sync_ms +=
+                std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+            CK(e);
         }
-        if ((uint32_t)(*d_status & 0xFFFFFFFFu) & kStatusTableFull) return SW_EINTERNAL;
-        g_stats.pairs += (int64_t)d_pairs[0];
-        g_stats.and_iters += (int64_t)d_pairs[1];
-        g_stats.rows_transposed += (int64_t)d_pairs[2];
-        // new levels; return the unused tail of each destination
+        if ((uint32_t)(*d_status & 0xFFFFFFFFu) & kStatusTableFull) {
+            (void)wait_stream(st);
+            return SW_EINTERNAL;
+        }
+        // new levels; return the unused tail of each destination.  A search
+        // with an empty level has run out of new sets: not synchronizing (its
+        // meet job has no tiles, so its memory can go at once)
         auto t_upd = std::chrono::steady_clock::now();
-        std::vector<int> met;
-        std::vector<unsigned long long> best;
         for (int t = 0; t < nj; ++t) {
             Sel &s = sel[t];
             Inst &x = I[s.id];
@@ -1012,19 +1055,44 @@ struct Engine {
             x.lev[s.d].push_back({s.dest, c, c, s.ge});
             x.dupl[s.d] = 1.0 - (double)c / (double)s.nc;
             x.stored[s.d] += c;
-            if (c == 0) {
-                finish(x, kFailed, SW_ENOTSYNC);
-            } else if (d_best[t] != ~0ull) {
-                met.push_back(s.id);
-                best.push_back(d_best[t]);
-            }
+            if (c == 0) finish(x, kFailed, SW_ENOTSYNC);
         }
         g_stats.update_ms +=
             std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t_upd).count();
+        // plan the next iteration while the meet kernel runs; a step planned
+        // for an instance that meets now is dropped below with its memory
+        auto t_plan = std::chrono::steady_clock::now();
+        plan(pending);
+        g_stats.select_ms +=
+            std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t_plan).count();
+        CK(wait_stream(st));
+        if (g_timing) {
+            g_stats.expand_ms += elapsed(g_ev.ev[0], g_ev.ev[1]);
+            g_stats.compact_ms += elapsed(g_ev.ev[1], g_ev.ev[2]);
+            g_stats.meet_ms += elapsed(g_ev.ev[3], g_ev.ev[4]);
+        }
+        g_stats.pairs += (int64_t)d_pairs[0];
+        g_stats.and_iters += (int64_t)d_pairs[1];
+        g_stats.rows_transposed += (int64_t)d_pairs[2];
+        std::vector<int> met;
+        std::vector<unsigned long long> best;
+        for (int t = 0; t < nj; ++t) {
+            if (I[sel[t].id].state != kActive || d_best[t] == ~0ull) continue;
+            met.push_back(sel[t].id);
+            best.push_back(d_best[t]);
+        }
         if (!met.empty()) {
             rc = recover_words(met, best);
             if (rc) return rc;
         }
+        // finished instances took their memory, planned steps included, with them
+        pending.erase(std::remove_if(pending.begin(), pending.end(),
+                                     [&](const Sel &s) {
+                                         if (I[s.id].state == kActive) return false;
+                                         planned[s.id] = 0;
+                                         return true;
+                                     }),
+                      pending.end());
         active.erase(std::remove_if(active.begin(), active.end(), [&](int id) { return I[id].state != kActive; }),
                      active.end());
         g_stats.arena_peak = std::max(g_stats.arena_peak, set_pool.used);

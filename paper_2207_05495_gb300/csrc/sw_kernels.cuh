@@ -19,6 +19,7 @@ namespace sw {
 constexpr uint64_t kEmpty = ~0ull;
 constexpr uint64_t kCand = 1ull << 62;  // slot value kCand + c: candidate c (this expansion)
 constexpr int kScanBlock = 512;         // candidates per block in flag/compact
+static_assert(kScanBlock % 32 == 0, "a warp of candidates must lie inside one job");
 constexpr int kScanThreads = 256;
 constexpr int kMaxProbe = 1 << 14;
 
@@ -329,19 +330,33 @@ __global__ void k_fill(const FillJob *__restrict__ jobs, uint64_t *__restrict__ 
         table[J.off + i] = kEmpty;
 }
 
+// The segment holding flat index t, searched in segs[lo .. hi].
+__device__ __forceinline__ int find_seg(const RehashSeg *__restrict__ segs, int lo, int hi, int64_t t) {
+    while (lo < hi) {
+        int mid = (lo + hi + 1) >> 1;
+        if (segs[mid].flat_off <= t) lo = mid; else hi = mid - 1;
+    }
+    return lo;
+}
+
 // Re-enters every stored set of a growing (instance, direction) into its
 // new, larger table.  Flat over all segments.
 template <int W>
 __global__ void k_rehash(const RehashSeg *__restrict__ segs, int nseg, int64_t total,
                          const uint64_t *__restrict__ sets, uint64_t *table, uint32_t *status) {
-    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total;
-         t += (int64_t)gridDim.x * blockDim.x) {
-        int lo = 0, hi = nseg - 1;
-        while (lo < hi) {
-            int mid = (lo + hi + 1) >> 1;
-            if (segs[mid].flat_off <= t) lo = mid; else hi = mid - 1;
-        }
-        const RehashSeg &S = segs[lo];
+    // a warp takes 32 consecutive indices; lanes 0 and 31 bound the segments
+    // they fall in, so every lane searches only that (usually one-entry) range
+    const int lane = threadIdx.x & 31;
+    for (int64_t base = blockIdx.x * (int64_t)blockDim.x + (threadIdx.x & ~31); base < total;
+         base += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t t = base + lane;
+        int a = 0, b = 0;
+        if (lane == 0) a = find_seg(segs, 0, nseg - 1, base);
+        if (lane == 31) b = find_seg(segs, 0, nseg - 1, min(t, total - 1));
+        a = __shfl_sync(0xffffffffu, a, 0);
+        b = __shfl_sync(0xffffffffu, b, 31);
+        if (t >= total) continue;
+        const RehashSeg &S = segs[find_seg(segs, a, b, t)];
         int64_t g = S.set_off + (t - S.flat_off);
         uint64_t s[W];
         load_set<W>(sets + g * W, s);
@@ -366,7 +381,13 @@ __global__ void __launch_bounds__(256) k_expand(
     int64_t *__restrict__ cand_slot, uint32_t *status) {
     for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < ncand;
          c += (int64_t)gridDim.x * blockDim.x) {
-        const ExpandJob &J = jobs[find_job_expand(jobs, njobs, c)];
+        // ncand is a multiple of kScanBlock and jobs start on kScanBlock
+        // boundaries, so the 32 candidates of a warp are all in range here
+        // and belong to one job: lane 0 finds it for the warp
+        int ji = 0;
+        if ((threadIdx.x & 31) == 0) ji = find_job_expand(jobs, njobs, c);
+        ji = __shfl_sync(0xffffffffu, ji, 0);
+        const ExpandJob &J = jobs[ji];
         int64_t local = c - J.cand_off;
         int64_t p = local / J.k;
         if (p >= J.parent_cnt) {  // padding up to the next job's block

@@ -203,6 +203,34 @@ def test_w_boundaries_and_max_states(sw, ws, meet_algo):
     check_sizes(d, fs, bs)
 
 
+def test_batch_in_waves_equals_roomy_batch(sw, ws):
+    # a workspace that holds every instance alone but not all of them at
+    # once: instances are set back (their memory freed) and rerun in later
+    # waves, and every result must equal the one from a roomy workspace.
+    # The smallest size of the list at which every instance fits alone is
+    # the one that forces set-backs; smaller ones may fail some instances
+    # with SW_ENOMEM, and the rest must still be right.
+    ds = gen.batch_random(64, 64, 128, 2, 500)
+    hs = [sw.load(d) for d in ds]
+    r_big, w_big = sw.sw_batch(hs, ws=ws)
+    assert sw.sw_last_stats()["waves"] == 1
+    tested = False
+    for mib in (16, 24, 32, 48, 64, 96, 128):
+        small = sw.workspace(mib << 20)
+        r_small, w_small = sw.sw_batch(hs, ws=small, raise_on_error=False)
+        st = sw.sw_last_stats()
+        ok = r_small >= 0
+        assert (r_small[ok] == r_big[ok]).all()
+        assert all(w_small[i] == w_big[i] for i in np.nonzero(ok)[0])
+        if ok.all():
+            assert st["evictions"] > 0 and st["waves"] > 1, (mib, st)
+            tested = True
+            break
+    assert tested
+    for i in (0, 17, 63):
+        assert (int(r_small[i]), w_small[i]) == oracle.bidir(ds[i])[:2]
+
+
 def test_word_cap_and_small_workspace(sw, ws):
     d = gen.cerny(6)
     h = sw.load(d)
