@@ -914,7 +914,10 @@ struct Engine {
     int iterate() {
         g_stats.iterations++;
         auto t_sel = std::chrono::steady_clock::now();
-        if (!ev_counts) CK(cudaEventCreateWithFlags(&ev_counts, cudaEventDisableTiming));
+        // the allocation-free entry point (pageable staging) creates no CUDA
+        // objects: it waits for the whole stream instead of a counts event
+        const bool counts_event = !g_pageable;
+        if (counts_event && !ev_counts) CK(cudaEventCreateWithFlags(&ev_counts, cudaEventDisableTiming));
         std::vector<Sel> sel;
         sel.swap(pending);
         plan(sel);  // instances without a planned step: new, or skipped for room
@@ -1023,7 +1026,7 @@ struct Engine {
         uint64_t *d_status = down + nj, *d_best = down + nj + 1, *d_pairs = down + 2 * nj + 1;
         CK(cudaMemcpyAsync(down, L.counts, nj * sizeof(uint64_t), cudaMemcpyDeviceToHost, st));
         CK(cudaMemcpyAsync(d_status, L.status, sizeof(uint32_t), cudaMemcpyDeviceToHost, st));
-        CK(cudaEventRecord(ev_counts, st));
+        if (counts_event) CK(cudaEventRecord(ev_counts, st));
         CK(cudaMemsetAsync(L.best, 0xFF, nj * sizeof(unsigned long long), st));
         CK(cudaMemsetAsync(L.pairs, 0, 3 * sizeof(unsigned long long), st));
         if (g_timing) CK(cudaEventRecord(g_ev.ev[3], st));
@@ -1032,12 +1035,14 @@ struct Engine {
         g_stats.meet_launches++;
         CK(cudaMemcpyAsync(d_best, L.best, nj * sizeof(unsigned long long), cudaMemcpyDeviceToHost, st));
         CK(cudaMemcpyAsync(d_pairs, L.pairs, 3 * sizeof(unsigned long long), cudaMemcpyDeviceToHost, st));
-        {
+        if (counts_event) {
             auto t0 = std::chrono::steady_clock::now();
             cudaError_t e = cudaEventSynchronize(ev_counts);
             g_stats.sync_ms +=
                 std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
             CK(e);
+        } else {
+            CK(wait_stream(st));
         }
         if ((uint32_t)(*d_status & 0xFFFFFFFFu) & kStatusTableFull) {
             (void)wait_stream(st);
