@@ -196,7 +196,8 @@ int32_t sw_batch_device(int32_t count, const int32_t *n, const int32_t *k,
  *   evictions:    instances set back to a later wave for lack of room.
  *   arena_peak:   most sets stored at once (all instances of a wave).
  *   and_iters:    warp-wide AND steps of the bitmap meet kernel (each ANDs
- *                 one 2048-bit state bitmap into the running intersection).
+ *                 one state's bitmap over a backward chunk, 2048, 4096 or
+ *                 8192 bits, into the running intersection).
  *   rows_transposed: backward sets transposed into per-state bitmaps by the
  *                 bitmap meet kernel (once per tile).
  *   words_ms:     device time of the word-recovery kernel (with timing on).
@@ -230,8 +231,10 @@ void sw_set_timing(int32_t on);
  *                         (even).
  *   meet_f_rows:          bitmap test: forward sets per tile (0 = 4096).
  *   meet_lane_words:      bitmap test: 0 = default chunk (4096 backward
- *                         sets for up to 192 states, else 2048); 4 = chunks
- *                         of 8192 sets (up to 192 states only).
+ *                         sets for up to 192 states, and for up to 438
+ *                         states when the bitmaps of the states that occur
+ *                         fit in shared memory; else 2048); 4 = chunks of
+ *                         8192 sets (up to 192 states only).
  *   dir_theta:            a forward step is taken when its predicted cost is
  *                         at most dir_theta times the backward step's.
  *   set_cost:             cost of producing one set, in pair tests (the
