@@ -483,6 +483,7 @@ def main():
     if rank == 0:
         print(json.dumps(line), flush=True)
     if world > 1:
+        barrier()  # rank 0 may still have been serving
         dist.destroy_process_group()
 
 
