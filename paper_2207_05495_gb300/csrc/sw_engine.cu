@@ -527,21 +527,22 @@ struct Ops {
         k_job_counts<<<(unsigned)((nj + 255) / 256), 256, 0, st>>>(jobs, nj, nblocks, L.block_off, L.counts);
         return cudaGetLastError();
     }
-    static cudaError_t meet(MeetJob *jobs, int nj, const MeetCfg &c, const Layout &L, cudaStream_t st) {
+    // tf_rows: forward rows per tile of the bitmap kernel for this launch
+    static cudaError_t meet(MeetJob *jobs, int nj, const MeetCfg &c, int tf_rows, const Layout &L, cudaStream_t st) {
         g_stats.launches += 2;
-        const int64_t TF = c.algo == 0 ? (int64_t)c.tf_rows : (int64_t)c.nt * c.R;
+        const int64_t TF = c.algo == 0 ? (int64_t)tf_rows : (int64_t)c.nt * c.R;
         k_meet_prep<<<1, 1024, 0, st>>>(jobs, nj, L.counts, TF, c.tb, L.ntiles);
         int64_t *ntiles = L.ntiles;
         if (c.algo == 0) {
             if constexpr (W <= 3)
                 if (c.lw == 4)
-                    return launch_meet_bm<W, 4, 1024>(jobs, nj, ntiles, c.tf_rows, c.n_cap, L.sets, L.perm, L.rec,
+                    return launch_meet_bm<W, 4, 1024>(jobs, nj, ntiles, tf_rows, c.n_cap, L.sets, L.perm, L.rec,
                                                       L.best, L.pairs, L.pairs + 1, L.pairs + 2, L.meta, st);
             if constexpr (W >= 4 && W <= 7)
                 if (c.lw == 2)
-                    return launch_meet_bm<W, 2, 1024>(jobs, nj, ntiles, c.tf_rows, c.n_cap, L.sets, L.perm, L.rec,
+                    return launch_meet_bm<W, 2, 1024>(jobs, nj, ntiles, tf_rows, c.n_cap, L.sets, L.perm, L.rec,
                                                       L.best, L.pairs, L.pairs + 1, L.pairs + 2, L.meta, st);
-            return launch_meet_bm<W, bm_lanes_words(W), kBmThreads>(jobs, nj, ntiles, c.tf_rows, c.n_cap, L.sets,
+            return launch_meet_bm<W, bm_lanes_words(W), kBmThreads>(jobs, nj, ntiles, tf_rows, c.n_cap, L.sets,
                                                                     L.perm, L.rec, L.best, L.pairs, L.pairs + 1,
                                                                     L.pairs + 2, L.meta, st);
         }
@@ -573,7 +574,7 @@ struct OpTable {
     cudaError_t (*rehash)(const RehashSeg *, int, int64_t, const Layout &, cudaStream_t);
     cudaError_t (*expand)(const ExpandJob *, int, int64_t, const Layout &, cudaStream_t);
     cudaError_t (*compact)(const ExpandJob *, int, int64_t, const Layout &, cudaStream_t);
-    cudaError_t (*meet)(MeetJob *, int, const MeetCfg &, const Layout &, cudaStream_t);
+    cudaError_t (*meet)(MeetJob *, int, const MeetCfg &, int, const Layout &, cudaStream_t);
     cudaError_t (*words)(const WordJob *, const int64_t *, int, uint8_t *, const Layout &, cudaStream_t);
 };
 
@@ -991,6 +992,27 @@ struct Engine {
         MeetJob *d_mj;
         MeetJob *mj = stg.take<MeetJob>(nj, &d_mj);
         if (!stg.ok) return SW_EINTERNAL;
+        // A launch with few tiles gets shorter forward tiles (down to 1024
+        // rows): more transposes, fewer idle SMs at its end.  The sizes of
+        // the new levels are predicted from their last duplicate ratios.
+        int tf_rows = mc.tf_rows;
+        if (mc.algo == 0 && tf_rows > 1024) {
+            std::vector<std::pair<double, double>> fb((size_t)nj);
+            for (int t = 0; t < nj; ++t) {
+                const Sel &s = sel[t];
+                const Inst &x = I[s.id];
+                const double grown = (double)s.nc * (1.0 - x.dupl[s.d]);
+                fb[t] = {s.d == 0 ? grown : (double)x.lev[0].back().cnt,
+                         s.d == 1 ? grown : (double)x.lev[1].back().cnt};
+            }
+            auto tiles_for = [&](int tfr) {
+                double n = 0;
+                for (const auto &v : fb) n += std::ceil(v.first / tfr) * std::ceil(v.second / mc.tb);
+                return n;
+            };
+            const double want = 8.0 * sm_count();
+            while (tf_rows > 1024 && tiles_for(tf_rows) < want) tf_rows /= 2;
+        }
         for (int t = 0; t < nj; ++t) {
             Sel &s = sel[t];
             Inst &x = I[s.id];
@@ -1030,7 +1052,7 @@ struct Engine {
         CK(cudaMemsetAsync(L.best, 0xFF, nj * sizeof(unsigned long long), st));
         CK(cudaMemsetAsync(L.pairs, 0, 3 * sizeof(unsigned long long), st));
         if (g_timing) CK(cudaEventRecord(g_ev.ev[3], st));
-        CK(ops.meet(d_mj, nj, mc, L, st));
+        CK(ops.meet(d_mj, nj, mc, tf_rows, L, st));
         if (g_timing) CK(cudaEventRecord(g_ev.ev[4], st));
         g_stats.meet_launches++;
         CK(cudaMemcpyAsync(d_best, L.best, nj * sizeof(unsigned long long), cudaMemcpyDeviceToHost, st));
