@@ -792,9 +792,9 @@ struct Engine {
         *taken = ok.size();
         if (ok.empty()) return SW_OK;
         int nj = (int)ok.size();
-        RootJob *d_rj;
-        FillJob *d_fj;
-        PreJob *d_pj;
+        RootJob *d_rj = nullptr;
+        FillJob *d_fj = nullptr;
+        PreJob *d_pj = nullptr;
         RootJob *rj = stg.take<RootJob>(nj, &d_rj);
         FillJob *fj = stg.take<FillJob>(2 * nj, &d_fj);
         PreJob *pj = stg.take<PreJob>(nj, &d_pj);
@@ -944,7 +944,7 @@ struct Engine {
         if (!stage_begin()) return SW_ECUDA;
         // jobs, table fills and rehash segments: one upload
         int nj = (int)sel.size();
-        ExpandJob *d_jobs;
+        ExpandJob *d_jobs = nullptr;
         ExpandJob *jobs = stg.take<ExpandJob>(nj, &d_jobs);
         if (!stg.ok) return SW_EINTERNAL;
         std::vector<FillJob> fills;
@@ -989,7 +989,7 @@ struct Engine {
         }
         // meet jobs: the size of the level each job produces is filled in on
         // the device (k_meet_prep), so the meet follows without a host sync
-        MeetJob *d_mj;
+        MeetJob *d_mj = nullptr;
         MeetJob *mj = stg.take<MeetJob>(nj, &d_mj);
         if (!stg.ok) return SW_EINTERNAL;
         // A launch with few tiles gets shorter forward tiles (down to 1024
@@ -1169,8 +1169,8 @@ struct Engine {
             }
             if (wj.empty()) continue;
             int nw = (int)wj.size();
-            WordJob *d_wj;
-            int64_t *d_bl;
+            WordJob *d_wj = nullptr;
+            int64_t *d_bl = nullptr;
             WordJob *hw = stg.take<WordJob>(nw, &d_wj);
             int64_t *hb = stg.take<int64_t>(std::max<size_t>(blev.size(), 3), &d_bl);
             if (!stg.ok) return SW_EINTERNAL;
