@@ -229,7 +229,9 @@ void sw_set_timing(int32_t on);
  *                         registers (1, 2, 4 or 8; 0 = pick by word count).
  *   meet_b_tile:          direct test: backward sets per shared-memory tile
  *                         (even).
- *   meet_f_rows:          bitmap test: forward sets per tile (0 = 4096).
+ *   meet_f_rows:          bitmap test: forward sets per tile (0 = 4096);
+ *                         a launch with fewer than 8 predicted tiles per SM
+ *                         halves it, down to 1024.
  *   meet_lane_words:      bitmap test: 0 = default chunk (4096 backward
  *                         sets for up to 192 states, and for up to 438
  *                         states when the bitmaps of the states that occur
