@@ -12,13 +12,23 @@ least shortest reset word of every instance.
   roofline      the meet kernel (the dominant kernel), integer-ALU bound:
                 int32 operations it performs (64 per 64-bit lane word of a
                 warp-wide AND step, 25 per 32-bit word of each transposed
-                backward row)
-                against 128 int32 lanes/SM x SMs x maximum SM clock.
+                backward row) against 128 int32 lanes/SM x SMs x maximum SM
+                clock.
+  roofline_hbm  the expansion and compaction kernels against the measured
+                HBM copy bandwidth: algorithmic bytes per candidate and per
+                stored set over their event time.
   serving       sw_server under Poisson arrivals (n~U[32,128], k in 2..4)
-                at 0.8x the batched capacity: p50/p99 latency, instances/s.
+                at 0.5, 0.8 and 1.0 x the batched capacity: p50/p99 latency,
+                instances/s, admissions while other searches ran.
   one_at_a_time sw_reset_threshold in a loop over a sample, and the batched
                 call on the same sample.
-  cpu_baseline  the CPU oracle (bidirectional) on a bounded sample, all cores.
+  cpu_baseline  the CPU oracle (bidirectional) on a fixed stratified sample
+                of the workload, every instance run to completion: all cores
+                and single-threaded.
+
+--workload hard300 / hard400 (/ hard500 / hard570): one hard random
+automaton (seed 0) searched alone, with r, time, peak sets, pairs/s, and the
+agreement of two direction schedules.
 
 --impl reference times the CPU oracle instead (the reference arm).
 """
@@ -83,10 +93,11 @@ def workload(name: str, rank: int = 0):
                                                   "instances": 1}
     if name == "cerny":
         return [gen.cerny(n) for n in range(16, 29)], {"workload": "Cerny automata n=16..28", "instances": 13}
-    if name == "hard300":
-        return [gen.random_automaton(300, 2, 0)], {
-            "workload": "hard single instance: random binary automaton n=300 k=2 seed 0, 5x64-bit bitsets",
-            "instances": 1}
+    if name in ("hard300", "hard400", "hard500", "hard570"):
+        n = int(name[4:])
+        return [gen.random_automaton(n, 2, 0)], {
+            "workload": f"hard single instance: random binary automaton n={n} k=2 seed 0, "
+                        f"{(n + 63) // 64}x64-bit bitsets", "instances": 1}
     raise SystemExit(f"unknown workload {name}")
 
 
@@ -149,77 +160,95 @@ def flush_l2(buf):
     buf.add_(1)  # touches 256 MiB, larger than the 129 MB L2
 
 
-def cpu_sample(ds, budget_s: float, cores: int):
-    """The oracle (bidirectional BFS) over the first instances of the
-    workload, all cores, until the time budget is spent; instances still
-    running at the hard cap are abandoned and not counted."""
-    import multiprocessing as mp
-    ctx = mp.get_context("spawn")
-    t0 = time.perf_counter()
-    done = 0
-    with ctx.Pool(cores, initializer=_oracle_init) as pool:
-        pending = []
-        nxt = 0
-        while True:
-            while nxt < len(ds) and len(pending) < 2 * cores and time.perf_counter() - t0 < budget_s:
-                pending.append(pool.apply_async(_oracle_one, (ds[nxt],)))
-                nxt += 1
-            still = []
-            for p in pending:
-                if p.ready():
-                    p.get()
-                    done += 1
-                else:
-                    still.append(p)
-            pending = still
-            el = time.perf_counter() - t0
-            if (el >= budget_s and not pending) or el >= 3 * budget_s or (nxt == len(ds) and not pending):
-                break
-            time.sleep(0.01)
-        elapsed = time.perf_counter() - t0
-        pool.terminate()
-    return done, elapsed
-
-
 def _oracle_init():
     sys.path.insert(0, ROOT)
 
 
 def _oracle_one(d):
+    """One oracle search (bidirectional BFS) in a worker; its own CPU time."""
     import oracle
-    return oracle.bidir(d)[0]
+    t0 = time.process_time()
+    r = oracle.bidir(d)[0]
+    return r, time.process_time() - t0
+
+
+def cpu_fixed_sample(pool, sample):
+    """Runs every automaton of `sample` through the oracle on the pool (one
+    process per core), each to completion; returns (wall seconds, summed
+    per-instance CPU seconds, r values)."""
+    t0 = time.perf_counter()
+    res = pool.map(_oracle_one, sample, chunksize=1)
+    wall = time.perf_counter() - t0
+    return wall, sum(t for _, t in res), [r for r, _ in res]
+
+
+def stratified_seeds(count: int, m: int):
+    """m seeds spread evenly over 0..count-1 (0, count/m, 2 count/m, ...)."""
+    return [i * count // m for i in range(m)]
+
+
+def oracle_pool(cores: int):
+    import multiprocessing as mp
+    import oracle
+    oracle.build()
+    return mp.get_context("spawn").Pool(cores, initializer=_oracle_init)
 
 
 def run_reference(args, ds, cfg, rank, world):
+    """The reference arm: the CPU oracle as it stands, on the machine's host
+    cores.  The oracle's cost per instance has a heavy tail (from 0.01 s to
+    over a minute on one core for this workload), so a step cannot hold an
+    unbiased sample and stay short; each step takes the next `cores`
+    instances (in seed order) of the workload's stratum n <= 100 and runs
+    every one to completion.  The stratum is declared in the line."""
     if rank != 0:
         return
     cores = os.cpu_count() or 1
-    import oracle
-    oracle.build()
-    for _ in range(args.warmup):
-        cpu_sample(ds, 2.0, cores)
-    tot_done, tot_t = 0, 0.0
-    for _ in range(args.steps):
-        d, t = cpu_sample(ds, args.cpu_budget, cores)
-        tot_done += d
-        tot_t += t
-    v = tot_done / tot_t if tot_t else 0.0
-    sample = f"first instances of the workload in seed order, {args.cpu_budget:.0f} s per step, {cores} processes"
+    stratum = [d for d in ds if d.shape[1] <= args.ref_n_max]
+    per = cores
+    need = per * (args.warmup + args.steps)
+    sample = [stratum[i % len(stratum)] for i in range(need)]
+    with oracle_pool(cores) as pool:
+        for s in range(args.warmup):
+            cpu_fixed_sample(pool, sample[s * per:(s + 1) * per])
+        tot_wall, tot_cpu, done = 0.0, 0.0, 0
+        for s in range(args.warmup, args.warmup + args.steps):
+            wall, cpu_s, rs = cpu_fixed_sample(pool, sample[s * per:(s + 1) * per])
+            tot_wall += wall
+            tot_cpu += cpu_s
+            done += len(rs)
+    v = done / tot_wall if tot_wall else 0.0
+    smp = (f"each step: the next {per} instances in seed order of the workload's stratum n <= {args.ref_n_max} "
+           f"({len(stratum)} of {len(ds)} instances), every one run to completion; {done} instances timed")
     line = {"impl": "reference", "metric": "exact-r instances/sec", "value": v, "unit": "instances/s",
-            "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot_t / args.steps,
+            "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot_wall / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
             "config": cfg,
-            "cpu_baseline": {"value": v, "unit": "instances/s", "cores": cores, "kind": "oracle", "sample": sample},
+            "cpu_baseline": {"value": v, "unit": "instances/s", "cores": cores, "kind": "oracle", "sample": smp,
+                             "single_thread": done / tot_cpu if tot_cpu else 0.0},
             "e2e": {"value": v, "unit": "instances/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
 
+def cpu_baseline_line(ds, m: int, cores: int):
+    """The oracle on a fixed stratified sample of the workload (m instances,
+    seeds spread evenly), every instance run to completion: all cores (one
+    process per core) and single-threaded (the summed per-instance CPU
+    times)."""
+    idx = stratified_seeds(len(ds), m)
+    with oracle_pool(min(cores, m)) as pool:
+        wall, cpu_s, rs = cpu_fixed_sample(pool, [ds[i] for i in idx])
+    return {"value": m / wall, "unit": "instances/s", "cores": min(cores, m), "kind": "oracle",
+            "single_thread": m / cpu_s if cpu_s else 0.0,
+            "sample": f"{m} instances at seeds {idx[0]}, {idx[1]}, ... {idx[-1]} (every {len(ds) // m}th), "
+                      f"each run to completion by the bidirectional oracle; wall {wall:.1f} s on "
+                      f"{min(cores, m)} processes, {cpu_s:.1f} s of summed CPU time"}
+
+
 def serve_bench(sw, torch, stream, args):
-    """Poisson arrivals into sw_server; latency = submit to poll."""
+    """Poisson arrivals into sw_server at lambda = 0.5, 0.8 and 1.0 x the
+    batched capacity on the same requests; latency = submit to poll."""
     m = args.serve_requests
-    rng_seed = 0xC5
-    arr = gen.splitmix64_block(rng_seed, 0, m)
-    u = (arr >> np.uint64(11)).astype(np.float64) / float(1 << 53)
     ds = []
     for i in range(m):
         st = gen._Stream(100000 + i)
@@ -232,43 +261,62 @@ def serve_bench(sw, torch, stream, args):
     sw.sw_batch(hs[:64], ws=ws, word_cap=4096)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    sw.sw_batch(hs, ws=ws, word_cap=4096)
+    r_batch, _ = sw.sw_batch(hs, ws=ws, word_cap=4096)
     torch.cuda.synchronize()
     cap = m / (time.perf_counter() - t0)
-    lam = 0.8 * cap
-    gaps = -np.log(1.0 - u) / lam
     del ws
-    srv = sw.Server(sw.workspace(16 << 30), n_max=128, k_max=4, max_requests=m, word_cap=4096)
-    sub_t = np.zeros(m)
-    lat = np.zeros(m)
-    got = 0
-    t_start = time.perf_counter()
-    next_t = t_start
-    i = 0
-    while got < m:
-        now = time.perf_counter()
-        while i < m and now >= next_t:
-            if srv.submit(hs[i], i) != 0:
-                break
-            sub_t[i] = time.perf_counter()
-            next_t += gaps[i]
-            i += 1
-        res = srv.poll()
-        while res is not None:
-            lat[res[0]] = time.perf_counter() - sub_t[res[0]]
-            if res[3] != 0:
-                raise RuntimeError(f"served request {res[0]} failed: {res[3]}")
-            got += 1
+    arr = gen.splitmix64_block(0xC5, 0, m)
+    u = (arr >> np.uint64(11)).astype(np.float64) / float(1 << 53)
+    runs = []
+    for frac in (0.5, 0.8, 1.0):
+        lam = frac * cap
+        gaps = -np.log(1.0 - u) / lam
+        srv = sw.Server(sw.workspace(16 << 30), n_max=128, k_max=4, max_requests=m, word_cap=4096)
+        sub_t = np.zeros(m)
+        lat = np.zeros(m)
+        got = 0
+        t_start = time.perf_counter()
+        next_t = t_start
+        i = 0
+        while got < m:
+            now = time.perf_counter()
+            while i < m and now >= next_t:
+                if srv.submit(hs[i], i) != 0:
+                    break
+                sub_t[i] = time.perf_counter()
+                next_t += gaps[i]
+                i += 1
             res = srv.poll()
-        if time.perf_counter() - t_start > 120:
-            raise RuntimeError("serving run exceeded 120 s")
-        time.sleep(0.0002)
-    total = time.perf_counter() - t_start
-    srv.close()
-    return {"requests": m, "arrivals": "Poisson, SplitMix64 seed 0xC5", "lambda_per_s": lam,
-            "batched_capacity_per_s": cap, "instances_per_s": m / total,
-            "p50_ms": float(np.percentile(lat, 50) * 1e3), "p99_ms": float(np.percentile(lat, 99) * 1e3),
-            "workload": "random automata n~U[32,128], k~U{2,3,4}"}
+            while res is not None:
+                lat[res[0]] = time.perf_counter() - sub_t[res[0]]
+                if res[3] != 0 or res[1] != r_batch[res[0]]:
+                    raise RuntimeError(f"served request {res[0]}: code {res[3]}, r {res[1]} != {r_batch[res[0]]}")
+                got += 1
+                res = srv.poll()
+            if time.perf_counter() - t_start > 120:
+                raise RuntimeError("serving run exceeded 120 s")
+            time.sleep(0.0002)
+        total = time.perf_counter() - t_start
+        st = srv.stats()
+        srv.close()
+        runs.append({"lambda_frac": frac, "lambda_per_s": lam, "instances_per_s": m / total,
+                     "p50_ms": float(np.percentile(lat, 50) * 1e3), "p99_ms": float(np.percentile(lat, 99) * 1e3),
+                     "admitted_while_running": st["admitted_while_1"], "max_active": st["max_active"]})
+    return {"requests": m, "arrivals": "Poisson, SplitMix64 seed 0xC5", "batched_capacity_per_s": cap,
+            "workload": "random automata n~U[32,128], k~U{2,3,4}", "runs": runs}
+
+
+def meet_roofline(stats, nsm):
+    """The meet kernel against the integer pipe: int32 operations it
+    performs (64 per 64-bit lane word of a warp-wide AND step, 25 per 32-bit
+    word of every transposed backward row) over its summed event time."""
+    meet_ms = sum(s["meet_ms"] for s in stats) / len(stats)
+    pairs = sum(s["pairs"] for s in stats) / len(stats)
+    iters = sum(s["and_iters"] for s in stats) / len(stats)
+    rows_t = sum(s["rows_transposed"] for s in stats) / len(stats)
+    launches = sum(s["meet_launches"] for s in stats) / len(stats)
+    lw = max(1, stats[-1]["meet_lane_words"])
+    return meet_ms, pairs, iters, rows_t, launches, lw
 
 
 def main():
@@ -277,9 +325,13 @@ def main():
     ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="c3", choices=["c3", "c1", "cerny", "hard300"])
+    ap.add_argument("--workload", default="c3",
+                    choices=["c3", "c1", "cerny", "hard300", "hard400", "hard500", "hard570"])
     ap.add_argument("--ws-gb", type=float, default=160.0)
-    ap.add_argument("--cpu-budget", type=float, default=20.0)
+    ap.add_argument("--cpu-sample", type=int, default=16,
+                    help="instances of the fixed stratified sample the CPU oracle runs to completion")
+    ap.add_argument("--ref-n-max", type=int, default=100,
+                    help="reference arm: the stratum (n <= this) its steps draw instances from")
     ap.add_argument("--one-sample", type=int, default=256)
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--count", type=int, default=0, help="use only the first COUNT instances (small cases)")
@@ -301,20 +353,20 @@ def main():
     cfg["l2"] = "flushed between steps (256 MiB write)"
     cfg["parallelism"] = f"replicas x{world} (independent instances per GPU)"
 
+    hard = args.workload.startswith("hard")
     if args.impl == "reference":
+        if hard:
+            if rank == 0:
+                print(json.dumps({"impl": "reference", "unavailable": "the CPU oracle does not finish a random "
+                                  "automaton of this size (about 1e14 candidate pairs at the meet)"}), flush=True)
+            return
         run_reference(args, ds, cfg, rank, world)
         return
 
     # CPU baseline first: its process pool is spawned before any CUDA work
     cpu = None
-    if rank == 0 and not args.no_cpu:
-        cores = os.cpu_count() or 1
-        import oracle
-        oracle.build()
-        done, el = cpu_sample(ds, args.cpu_budget, cores)
-        cpu = {"value": done / el if el else 0.0, "unit": "instances/s", "cores": cores, "kind": "oracle",
-               "sample": f"first {done} instances of the workload in seed order (bidirectional oracle, "
-                         f"{cores} processes, {el:.1f} s)"}
+    if rank == 0 and not args.no_cpu and not hard:
+        cpu = cpu_baseline_line(ds, min(args.cpu_sample, len(ds)), os.cpu_count() or 1)
 
     import torch
     import torch.distributed as dist
@@ -341,6 +393,19 @@ def main():
         sw.sw_set_options(o)
     if not cfg["options"]:
         cfg["options"] = "library defaults"
+    props = torch.cuda.get_device_properties(local)
+    nsm = props.multi_processor_count
+    peak = INT32_LANES_PER_SM * nsm * SM_MAX_MHZ_FALLBACK * 1e6 / 1e12
+    smem_peak = SMEM_BYTES_PER_CLK_SM * nsm * SM_MAX_MHZ_FALLBACK * 1e6 / 1e12
+    hbm_peak = hbm_peak_gbs()
+    if hard:
+        line = run_hard(args, ds[0], cfg, sw, torch, local, world, peak, nsm)
+        if rank == 0:
+            print(json.dumps(line), flush=True)
+        if world > 1:
+            dist.destroy_process_group()
+        return
+
     ns = np.array([d.shape[1] for d in ds], np.int32)
     ks = np.array([d.shape[0] for d in ds], np.int32)
     W = int(max((int(n) + 63) // 64 for n in ns))
@@ -413,6 +478,11 @@ def main():
     e2e_s = float(np.mean(e2e_t))
     h2d = int(sum(d.size for d in ds) * 2)  # uint16 transition tables
     d2h = int(4 * count + int(r.sum()))
+    # sets the compaction stored per step (every computed level but the roots)
+    survivors = 0
+    for h in hs:
+        fs, bs = sw.sw_level_sizes(h)
+        survivors += sum(fs[1:]) + sum(bs[1:])
 
     # one at a time vs batched, on the same sample
     m = min(args.one_sample, count)
@@ -427,23 +497,26 @@ def main():
     torch.cuda.synchronize()
     batch_m_s = time.perf_counter() - t0
 
-    # roofline of the meet kernel
     st = stats[-1]
-    meet_ms = sum(s["meet_ms"] for s in stats) / len(stats)
-    pairs = sum(s["pairs"] for s in stats) / len(stats)
-    iters = sum(s["and_iters"] for s in stats) / len(stats)
-    rows_t = sum(s["rows_transposed"] for s in stats) / len(stats)
-    launches = sum(s["meet_launches"] for s in stats) / len(stats)
-    lw = 2 if W <= 3 else 1  # 64-bit words of the running AND per lane
+    meet_ms, pairs, iters, rows_t, launches, lw = meet_roofline(stats, nsm)
     ops = iters * 64 * lw + rows_t * 2 * W * 25
     smem_bytes = iters * 256 * lw + rows_t * 8 * W
     sec = meet_ms * 1e-3
     achieved = ops / sec / 1e12 if sec > 0 else 0.0
-    props = torch.cuda.get_device_properties(local)
     clocks = clk.summary()
-    nsm = props.multi_processor_count
-    peak = INT32_LANES_PER_SM * nsm * SM_MAX_MHZ_FALLBACK * 1e6 / 1e12
-    smem_peak = SMEM_BYTES_PER_CLK_SM * nsm * SM_MAX_MHZ_FALLBACK * 1e6 / 1e12
+    cand = sum(s["candidates"] for s in stats) / len(stats)
+    expand_ms = sum(s["expand_ms"] for s in stats) / len(stats)
+    compact_ms = sum(s["compact_ms"] for s in stats) / len(stats)
+    k0 = float(np.mean(ks))
+    hbm = {
+        "k_expand": hbm_line(expand_ms, cand * (8 * W / k0 + 8 * W + 8 + 8), hbm_peak,
+                             "per candidate: 8W/k B of parent read, 8W B written, an 8 B table slot read "
+                             "(CAS), 8 B slot index written"),
+        "compaction": hbm_line(compact_ms, cand * 18 + survivors * (24 * W + 36), hbm_peak,
+                               "per candidate: 8 B slot index and 8 B table slot read, 1 B flag written and "
+                               "read; per stored set: 8W B read twice and written once, 8 B parent link, 16 B "
+                               "record, 4 B permutation entry and 8 B table slot written"),
+    }
     serving = serve_bench(sw, torch, stream, args) if rank == 0 and not args.no_serve else None
     line = {
         "metric": "exact-r instances/sec", "value": value, "unit": "instances/s", "n_gpus": world,
@@ -453,26 +526,28 @@ def main():
                 "d2h_bytes_per_step": d2h},
         "roofline": {"bound": "alu", "kernel": "k_meet_bm", "achieved": achieved, "peak": peak, "unit": "Tops/s",
                      "frac": achieved / peak if peak else None,
-                     "traffic": MEET_DRAM_BYTES_PER_ROW * rows_t / max(launches, 1) if args.workload == "c3" else None,
+                     "traffic": (MEET_DRAM_BYTES_PER_ROW * rows_t / max(launches, 1)
+                                 if args.workload == "c3" and MEET_DRAM_BYTES_PER_ROW else None),
                      "traffic_basis": "ncu dram__bytes_read.sum + dram__bytes_write.sum per transposed backward row, "
                                       "measured on the first 512 automata of this workload, times rows per launch",
-                     "work": "int32 ops executed: 64 per 64-bit lane word per warp AND step + 25 per transposed 32-bit row word",
-                     "and_steps_per_step": iters, "rows_transposed_per_step": rows_t,
+                     "work": "int32 ops executed: 64 per 64-bit lane word per warp AND step + 25 per transposed "
+                             "32-bit row word",
+                     "lane_words": lw, "and_steps_per_step": iters, "rows_transposed_per_step": rows_t,
                      "smem_tbs": smem_bytes / sec / 1e12 if sec > 0 else 0.0, "smem_peak_tbs": smem_peak,
                      "pairs_per_step": pairs, "pairs_per_sec_in_kernel": pairs / sec if sec > 0 else 0.0,
                      "launches_per_step": launches, "avg_launch_ms": meet_ms / max(launches, 1),
                      "peak_basis": f"{INT32_LANES_PER_SM} int32 lanes/SM x {nsm} SMs x "
                                    f"{SM_MAX_MHZ_FALLBACK:.0f} MHz (max SM clock)"},
+        "roofline_hbm": hbm,
         "subset_checks_per_sec": pairs / (ms * 1e-3),
-        "kernel_ms_per_step": {"meet": meet_ms, "expand": sum(s["expand_ms"] for s in stats) / len(stats),
-                               "compact": sum(s["compact_ms"] for s in stats) / len(stats),
+        "kernel_ms_per_step": {"meet": meet_ms, "expand": expand_ms, "compact": compact_ms,
                                "words": sum(s["words_ms"] for s in stats) / len(stats),
                                "host_wall": sum(s["run_ms"] for s in stats) / len(stats),
                                "host_wait": sum(s["sync_ms"] for s in stats) / len(stats),
                                "host_select": sum(s["select_ms"] for s in stats) / len(stats),
                                "host_update": sum(s["update_ms"] for s in stats) / len(stats)},
         "iterations_per_step": st["iterations"], "waves": st["waves"], "evictions": st["evictions"],
-        "arena_peak_sets": st["arena_peak"],
+        "arena_peak_sets": st["arena_peak"], "candidates_per_step": cand, "stored_sets_per_step": survivors,
         "one_at_a_time": {"value": m / one_s, "unit": "instances/s", "sample": f"first {m} instances",
                           "batched_same_sample": m / batch_m_s},
         "serving": serving,
@@ -485,6 +560,89 @@ def main():
     if world > 1:
         barrier()  # rank 0 may still have been serving
         dist.destroy_process_group()
+
+
+def hbm_peak_gbs():
+    try:
+        with open(PEAKS_FILE) as fh:
+            return float(json.load(fh)["hbm_gbs"]), "measured"
+    except (OSError, KeyError, ValueError):
+        return 6800.0, "fallback"
+
+
+def hbm_line(ms, nbytes, peak, basis):
+    """An HBM-bound kernel's algorithmic bytes per step over its event time."""
+    p, src = peak
+    gbs = nbytes / (ms * 1e-3) / 1e9 if ms > 0 else 0.0
+    return {"bound": "hbm", "achieved": gbs, "peak": p, "unit": "GB/s", "frac": gbs / p if p else None,
+            "peak_basis": f"{src} copy bandwidth", "bytes_per_step": nbytes, "ms_per_step": ms, "traffic": None,
+            "bytes_basis": basis}
+
+
+def run_hard(args, d, cfg, sw, torch, local, world, peak, nsm):
+    """A hard single instance: W warm-up and K timed searches with the
+    library's direction rule, then one with "expand the smaller side"
+    (a huge SetCost); both must return the same r and word."""
+    n = d.shape[1]
+    torch.cuda.empty_cache()
+    free, _ = torch.cuda.mem_get_info()
+    ws = sw.workspace(min(int(args.ws_gb * (1 << 30)), int(free * 0.8)))
+    stream = torch.cuda.Stream()
+    h = sw.load(d)
+
+    def once():
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        r, w = sw.sw_reset_threshold(h, stream=stream, ws=ws, word_cap=4096)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return r, w, e0.elapsed_time(e1) * 1e-3, sw.sw_last_stats(), sw.sw_level_sizes(h)
+
+    for _ in range(args.warmup):
+        once()
+    sw.sw_set_timing(True)
+    runs = []
+    with Clocks(local) as clk:
+        for _ in range(args.steps):
+            runs.append(once())
+    r, w, _, st, (fs, bs) = runs[-1]
+    sec = float(np.mean([x[2] for x in runs]))
+    old = sw.sw_get_options()
+    o = sw.sw_get_options()
+    o.set_cost = 1e9
+    sw.sw_set_options(o)
+    r2, w2, sec2, st2, (fs2, bs2) = once()
+    sw.sw_set_options(old)
+    sw.sw_set_timing(False)
+    states = np.arange(n)
+    for a in w:
+        states = d[a][states]
+    m_ = min(len(fs), len(fs2))
+    mb = min(len(bs), len(bs2))
+    agree = (r, w) == (r2, w2) and fs[:m_] == fs2[:m_] and bs[:mb] == bs2[:mb]
+    meet_ms, pairs, iters, rows_t, launches, lw = meet_roofline([x[3] for x in runs], nsm)
+    W = (n + 63) // 64
+    ops = iters * 64 * lw + rows_t * 2 * W * 25
+    achieved = ops / (meet_ms * 1e-3) / 1e12 if meet_ms > 0 else 0.0
+    return {
+        "metric": "exact-r instances/sec", "value": 1.0 / sec, "unit": "instances/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": sec * 1e3, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic", "config": cfg,
+        "e2e": {"value": 1.0 / sec, "unit": "instances/s", "h2d_bytes_per_step": int(d.size * 2),
+                "d2h_bytes_per_step": 4 + r},
+        "hard": {"n": n, "r": r, "word_resets": bool(len(np.unique(states)) == 1 and len(w) == r),
+                 "seconds": sec, "fwd_levels": len(fs) - 1, "bwd_levels": len(bs) - 1,
+                 "peak_sets": st["arena_peak"], "pairs": st["pairs"], "pairs_per_s": st["pairs"] / sec,
+                 "meet_ms": meet_ms, "expand_ms": st["expand_ms"], "compact_ms": st["compact_ms"],
+                 "balanced_schedule": {"r": r2, "seconds": sec2, "peak_sets": st2["arena_peak"],
+                                       "pairs": st2["pairs"], "fwd_levels": len(fs2) - 1,
+                                       "bwd_levels": len(bs2) - 1},
+                 "schedules_agree": bool(agree)},
+        "roofline": {"bound": "alu", "kernel": "k_meet_bm", "achieved": achieved, "peak": peak, "unit": "Tops/s",
+                     "frac": achieved / peak if peak else None, "traffic": None, "lane_words": lw},
+        "clocks": clk.summary(), "gpu_launches": int(st["launches"]), "cpu_baseline": None,
+    }
 
 
 if __name__ == "__main__":

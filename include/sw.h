@@ -124,12 +124,26 @@ int32_t sw_reset_threshold(sw_handle h, void *stream, void *workspace, size_t ws
  * small"); use sw_reset_threshold with a larger workspace for those.
  *
  * The first call on each device looks up the scratch's device address
- * (cudaGetSymbolAddress) with that device current; make that first call
- * before any stream capture begins.  Every call on a device shares the one
- * scratch array and starts by re-initialising what it reads, so results
- * never depend on an earlier call; but two calls whose GPU work overlaps
- * (different threads or streams at the same time) race on it and must be
- * serialised by the caller.
+ * (cudaGetSymbolAddress) with that device current.  Under CUDA's lazy
+ * module loading that lookup (or this library's first kernel launch) is
+ * also when the device reserves the 64 MiB array, so a caller whose
+ * allocator will later take the whole GPU must make its first call before
+ * that allocator reserves memory: one call at start-up with any automaton
+ * (a one-state automaton is enough) loads the module and fixes the address.
+ * The call copies through pageable host memory and synchronises `stream`,
+ * so it must not be called while `stream` is being captured into a CUDA
+ * graph (nor, with a NULL stream, while any capture is in progress).  It
+ * also gives up the overlap of the host's planning with the meet kernel
+ * that sw_reset_threshold has: it is meant for callers that cannot
+ * allocate, not for throughput.
+ *
+ * Every call on a device shares the one scratch array and starts by
+ * re-initialising what it reads, so results never depend on an earlier
+ * call; but two calls whose GPU work overlaps (different threads or streams
+ * at the same time) race on it and must be serialised by the caller.
+ * Every valid automaton passes the size check on entry (its starting state
+ * is a few MiB at most); SW_ENOMEM comes from the search itself once its
+ * levels and tables have filled the array.
  */
 #define SW_STATIC_SCRATCH_BYTES (64u << 20)
 int32_t sw_reset_threshold_static(sw_handle h, void *stream, int32_t *r, uint8_t *word,
@@ -206,13 +220,18 @@ int32_t sw_batch_device(int32_t count, const int32_t *n, const int32_t *k,
  *                 host work between launches.
  *   select_ms, update_ms: host time choosing each iteration's jobs and
  *                 recording the levels they produced.
+ *   meet_lane_words: 64-bit words of the running AND each lane holds in the
+ *                 bitmap meet kernel of that search (1, 2 or 4; 0 when the
+ *                 direct test ran), so that one AND step ANDs 64 *
+ *                 meet_lane_words 32-bit words per warp.
  */
 int32_t sw_last_stats(int64_t *pairs, int64_t *candidates, int32_t *iterations,
                       double *meet_ms, double *expand_ms, double *compact_ms,
                       int32_t *meet_launches, int64_t *launches, int32_t *waves,
                       int32_t *evictions, int64_t *arena_peak, int64_t *and_iters,
                       int64_t *rows_transposed, double *words_ms, double *run_ms,
-                      double *sync_ms, double *select_ms, double *update_ms);
+                      double *sync_ms, double *select_ms, double *update_ms,
+                      int32_t *meet_lane_words);
 
 /* Enables (1) or disables (0) per-kernel CUDA-event timing for later
  * searches on the calling thread. */
@@ -288,6 +307,18 @@ int32_t sw_server_submit(sw_server *srv, sw_handle h, uint64_t req_id);
 int32_t sw_server_poll(sw_server *srv, uint64_t *req_id, int32_t *r, uint8_t *word,
                        int32_t word_cap, int32_t *code);
 int32_t sw_server_pending(sw_server *srv, int32_t *queued, int32_t *active, int32_t *finished);
+
+/*
+ * Counters of a server since its creation (no counterpart in the paper;
+ * they show that the batching is continuous).  admitted: requests admitted
+ * into the engine; admitted_while_1 / admitted_while_2: those admitted
+ * while at least one / at least two earlier searches were mid-run (their
+ * levels on the device, between two iterations); max_active: the most
+ * searches advanced by one iteration's launches; iterations: iterations
+ * run.  Any pointer may be NULL.  SW_EINVAL if srv is NULL.
+ */
+int32_t sw_server_stats(sw_server *srv, int64_t *admitted, int64_t *admitted_while_1,
+                        int64_t *admitted_while_2, int32_t *max_active, int64_t *iterations);
 void sw_server_destroy(sw_server *srv);
 
 #ifdef __cplusplus

@@ -35,10 +35,11 @@ class OracleError(RuntimeError):
 
 
 def build(force: bool = False) -> str:
-    """Compile liboracle.so with gcc (plain -O2, portable: no -march)."""
+    """Compile liboracle.so with gcc -O3 (portable: no -march, so that it
+    builds and gives the same results on x86 and Arm hosts)."""
     if force or not os.path.exists(_LIB_PATH) or os.path.getmtime(_LIB_PATH) < os.path.getmtime(_SRC):
         tmp = _LIB_PATH + f".tmp{os.getpid()}"
-        subprocess.check_call(["gcc", "-O2", "-std=c11", "-shared", "-fPIC", "-o", tmp, _SRC])
+        subprocess.check_call(["gcc", "-O3", "-std=c11", "-shared", "-fPIC", "-o", tmp, _SRC])
         os.replace(tmp, _LIB_PATH)
     return _LIB_PATH
 

@@ -51,6 +51,7 @@ struct Stats {
     int64_t launches = 0;  // every kernel launch of the search
     int32_t waves = 0, evictions = 0;
     int64_t arena_peak = 0;  // most sets stored at once
+    int32_t meet_lw = 0;     // bitmap meet: 64-bit words of the running AND per lane (0: direct test)
 };
 
 thread_local int32_t g_last_error = SW_OK;
@@ -662,6 +663,7 @@ struct Engine {
         : W(W_), st(s), L(lay), I(insts) {
         ops = ops_for(W);
         mc = meet_cfg(W, n_max);
+        g_stats.meet_lw = mc.algo == 0 ? mc.lw : 0;
         set_pool.init(L.cap_sets);
         tab_pool.init(L.cap_table);
     }
@@ -1304,6 +1306,10 @@ struct sw_server {
     std::atomic<bool> stop{false};
     std::atomic<int32_t> fatal{SW_OK};
     std::atomic<int32_t> n_active{0}, n_queued{0};
+    // evidence of continuous batching: requests admitted while other
+    // searches were mid-run, and the most searches advanced in one iteration
+    std::atomic<int64_t> admitted{0}, admitted_1{0}, admitted_2{0}, iterations{0};
+    std::atomic<int32_t> max_active{0};
     std::thread worker;
 
     void loop();
@@ -1383,9 +1389,13 @@ int sw_server::admit_some() {
     }
     if (!ids.empty()) {
         size_t taken = 0;
+        const size_t running = eng->active.size();  // searches already mid-run
         int rc = eng->admit(ids, 0, &taken);
         if (rc) return rc;
         queue.erase(queue.begin(), queue.begin() + (std::ptrdiff_t)taken);
+        admitted += (int64_t)taken;
+        if (running >= 1) admitted_1 += (int64_t)taken;
+        if (running >= 2) admitted_2 += (int64_t)taken;
     }
     n_queued = (int32_t)queue.size();
     return SW_OK;
@@ -1429,6 +1439,8 @@ void sw_server::loop() {
             cv.wait_for(lk, std::chrono::milliseconds(2), [&] { return stop || !incoming.empty(); });
             continue;
         }
+        max_active = std::max<int32_t>(max_active.load(), (int32_t)eng->active.size());
+        iterations++;
         rc = eng->iterate();
         if (rc) {
             fatal = rc;
@@ -1715,7 +1727,7 @@ int32_t sw_last_stats(int64_t *pairs, int64_t *candidates, int32_t *iterations, 
                       double *expand_ms, double *compact_ms, int32_t *meet_launches, int64_t *launches,
                       int32_t *waves, int32_t *evictions, int64_t *arena_peak, int64_t *and_iters,
                       int64_t *rows_transposed, double *words_ms, double *run_ms, double *sync_ms,
-                      double *select_ms, double *update_ms) {
+                      double *select_ms, double *update_ms, int32_t *meet_lane_words) {
     if (pairs) *pairs = g_stats.pairs;
     if (candidates) *candidates = g_stats.candidates;
     if (iterations) *iterations = g_stats.iterations;
@@ -1831,6 +1843,17 @@ int32_t sw_server_pending(sw_server *s, int32_t *queued, int32_t *active, int32_
     if (active) *active = s->n_active;
     if (finished) *finished = (int32_t)s->done.size();
     return s->fatal;
+}
+
+int32_t sw_server_stats(sw_server *s, int64_t *admitted, int64_t *admitted_while_1, int64_t *admitted_while_2,
+                        int32_t *max_active, int64_t *iterations) {
+    if (!s) return fail(SW_EINVAL);
+    if (admitted) *admitted = s->admitted;
+    if (admitted_while_1) *admitted_while_1 = s->admitted_1;
+    if (admitted_while_2) *admitted_while_2 = s->admitted_2;
+    if (max_active) *max_active = s->max_active;
+    if (iterations) *iterations = s->iterations;
+    return SW_OK;
 }
 
 void sw_server_destroy(sw_server *s) {

@@ -63,7 +63,7 @@ def lib():
         L.sw_batch.restype = i32
         L.sw_batch_device.argtypes = [i32, p, p, p, p, p, p, sz, p, p, p, i64]
         L.sw_batch_device.restype = i32
-        L.sw_last_stats.argtypes = [p] * 18
+        L.sw_last_stats.argtypes = [p] * 19
         L.sw_last_stats.restype = i32
         L.sw_set_timing.argtypes = [i32]
         L.sw_set_timing.restype = None
@@ -81,6 +81,8 @@ def lib():
         L.sw_server_poll.restype = i32
         L.sw_server_pending.argtypes = [p, p, p, p]
         L.sw_server_pending.restype = i32
+        L.sw_server_stats.argtypes = [p, p, p, p, p, p]
+        L.sw_server_stats.restype = i32
         L.sw_server_destroy.argtypes = [p]
         L.sw_server_destroy.restype = None
         _lib = L
@@ -222,16 +224,18 @@ def sw_last_stats() -> dict:
     sel, upd = ctypes.c_double(), ctypes.c_double()
     it, ml, wv, ev = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32()
     mm, em, cm = ctypes.c_double(), ctypes.c_double(), ctypes.c_double()
+    lw = ctypes.c_int32()
     lib().sw_last_stats(ctypes.byref(pairs), ctypes.byref(cand), ctypes.byref(it), ctypes.byref(mm),
                         ctypes.byref(em), ctypes.byref(cm), ctypes.byref(ml), ctypes.byref(launches),
                         ctypes.byref(wv), ctypes.byref(ev), ctypes.byref(peak), ctypes.byref(iters),
                         ctypes.byref(rows), ctypes.byref(wms), ctypes.byref(rms), ctypes.byref(sms),
-                        ctypes.byref(sel), ctypes.byref(upd))
+                        ctypes.byref(sel), ctypes.byref(upd), ctypes.byref(lw))
     return {"pairs": pairs.value, "candidates": cand.value, "iterations": it.value, "meet_ms": mm.value,
             "expand_ms": em.value, "compact_ms": cm.value, "meet_launches": ml.value,
             "launches": launches.value, "waves": wv.value, "evictions": ev.value, "arena_peak": peak.value,
             "and_iters": iters.value, "rows_transposed": rows.value, "words_ms": wms.value,
-            "run_ms": rms.value, "sync_ms": sms.value, "select_ms": sel.value, "update_ms": upd.value}
+            "run_ms": rms.value, "sync_ms": sms.value, "select_ms": sel.value, "update_ms": upd.value,
+            "meet_lane_words": lw.value}
 
 
 def sw_set_timing(on: bool) -> None:
@@ -290,6 +294,16 @@ class Server:
         if rc != SW_OK:
             raise SwError(rc, "sw_server_pending")
         return q.value, a.value, f.value
+
+    def stats(self) -> dict:
+        a, a1, a2, it = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int64()
+        mx = ctypes.c_int32()
+        rc = lib().sw_server_stats(ctypes.c_void_p(self.ptr), ctypes.byref(a), ctypes.byref(a1), ctypes.byref(a2),
+                                   ctypes.byref(mx), ctypes.byref(it))
+        if rc != SW_OK:
+            raise SwError(rc, "sw_server_stats")
+        return {"admitted": a.value, "admitted_while_1": a1.value, "admitted_while_2": a2.value,
+                "max_active": mx.value, "iterations": it.value}
 
     def close(self):
         if getattr(self, "ptr", None):

@@ -46,3 +46,50 @@ def test_workloads_have_the_stated_shapes():
     assert len(ds) == 1 and ds[0].shape == (2, 300)
     ds, cfg = bench.workload("cerny")
     assert [d.shape[1] for d in ds] == list(range(16, 29))
+
+
+def test_workloads_hard400_shape():
+    ds, cfg = bench.workload("hard400")
+    assert len(ds) == 1 and ds[0].shape == (2, 400) and "7x64-bit" in cfg["workload"]
+
+
+def test_stratified_seeds_spread_evenly():
+    assert bench.stratified_seeds(4096, 16) == list(range(0, 4096, 256))
+    assert bench.stratified_seeds(10, 3) == [0, 3, 6]
+
+
+def _run_bench(*argv):
+    import json
+    import subprocess
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    out = subprocess.run([sys.executable, os.path.join(root, "bench.py"), *argv], capture_output=True, text=True,
+                         timeout=600, check=True).stdout
+    lines = [ln for ln in out.splitlines() if ln.startswith("{")]
+    assert len(lines) == 1, out
+    return json.loads(lines[0])
+
+
+def test_reference_arm_runs_every_sampled_instance_to_completion():
+    # the reference arm on the CPU: W warm-up and K timed steps of the
+    # oracle over the declared stratum; no GPU is touched
+    line = _run_bench("--impl", "reference", "--workload", "c1", "--steps", "2", "--warmup", "1")
+    cores = os.cpu_count() or 1
+    assert line["impl"] == "reference" and line["steps"] == 2 and line["value"] > 0
+    assert line["cpu_baseline"]["cores"] == cores
+    assert f"{2 * cores} instances timed" in line["cpu_baseline"]["sample"]
+    assert line["cpu_baseline"]["single_thread"] > 0
+    assert line["e2e"]["value"] == line["value"]
+
+
+def test_reference_arm_hard_instance_is_unavailable():
+    line = _run_bench("--impl", "reference", "--workload", "hard300")
+    assert line["impl"] == "reference" and "unavailable" in line
+
+
+def test_cpu_baseline_line_counts_every_instance():
+    from paper_2207_05495_gb300 import gen
+    ds = [gen.random_automaton(12 + i, 2, i) for i in range(8)]
+    cpu = bench.cpu_baseline_line(ds, 4, 2)
+    assert cpu["cores"] == 2 and cpu["kind"] == "oracle"
+    assert cpu["value"] > 0 and cpu["single_thread"] > 0
+    assert "seeds 0, 2, ... 6" in cpu["sample"]

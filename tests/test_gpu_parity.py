@@ -281,19 +281,26 @@ def test_batch_device_not_synchronizing(sw, ws):
 
 def test_server_results_equal_alone(sw):
     """Requests arriving while others run are admitted into the running
-    iterations; each result equals the one computed alone."""
+    iterations (continuous batching); each result equals the one computed
+    alone and the oracle's.  Two long Cerny searches (528 and 729 levels)
+    start first, so the later arrivals can only overlap with them if the
+    server admits requests mid-run; its counters must show admissions while
+    at least two searches were in progress, which a server that ran its
+    requests one at a time could not show."""
     import time
     rng = np.random.default_rng(77)
-    ds = []
+    ds = [gen.cerny(24), gen.cerny(28)]
     for i in range(48):
-        n = int(rng.integers(16, 90))
         k = int(rng.choice([2, 3, 4]))
+        n = int(rng.integers(16, {2: 90, 3: 64, 4: 48}[k]))
         ds.append(gen.random_automaton(n, k, 9000 + i))
     ds.append(gen.cerny(12))
     ds.append(np.zeros((2, 1), np.int32))
+    want = [oracle.bidir(d)[:2] for d in ds]
     hs = [sw.load(d) for d in ds]
     ws_alone = sw.workspace(256 << 20)
     alone = [sw.sw_reset_threshold(h, ws=ws_alone) for h in hs]
+    assert alone == want
     srv = sw.Server(sw.workspace(1 << 30), n_max=128, k_max=4, max_requests=64)
     got = {}
     try:
@@ -311,9 +318,12 @@ def test_server_results_equal_alone(sw):
                 time.sleep(0.001)
             else:
                 got[res[0]] = res
+        stats = srv.stats()
     finally:
         srv.close()
     assert len(got) == len(hs)
     for i in range(len(hs)):
         req, r, w, code = got[i]
-        assert code == 0 and (r, w) == alone[i], i
+        assert code == 0 and (r, w) == alone[i] == want[i], i
+    assert stats["admitted_while_2"] >= 1, stats
+    assert stats["max_active"] >= 3, stats
