@@ -55,8 +55,10 @@ def _load():
         lib.oracle_level_sizes.argtypes = [ctypes.c_int, ctypes.c_int, p, ctypes.c_int, i32, i64, p]
         lib.oracle_bidir.argtypes = [ctypes.c_int, ctypes.c_int, p, i64, p, p, i32, p, p, p, p, i32]
         lib.oracle_is_synchronizing.argtypes = [ctypes.c_int, ctypes.c_int, p]
+        lib.oracle_reduced_level_sizes.argtypes = [ctypes.c_int, ctypes.c_int, p, ctypes.c_int, i32, i64, p]
+        lib.oracle_bidir_reduced.argtypes = [ctypes.c_int, ctypes.c_int, p, i64, i32, p, p, i32, p, p, p, p, i32]
         for f in (lib.oracle_brute, lib.oracle_forward, lib.oracle_level_sizes, lib.oracle_bidir,
-                  lib.oracle_is_synchronizing):
+                  lib.oracle_is_synchronizing, lib.oracle_reduced_level_sizes, lib.oracle_bidir_reduced):
             f.restype = ctypes.c_int
         _lib = lib
     return _lib
@@ -124,6 +126,38 @@ def bidir(delta, max_sets: int = 50_000_000, word_cap: int = 1 << 20):
                               _ptr(bs), _ptr(nb), cap)
     if rc:
         raise OracleError(rc, "oracle_bidir")
+    return int(r[0]), w[: r[0]].tolist(), fs[: nf[0]].tolist(), bs[: nb[0]].tolist()
+
+
+def reduced_level_sizes(delta, direction: int, depth: int, max_sets: int = 50_000_000):
+    """Sizes of the levels 0..depth of one direction under the inclusion
+    reductions of Alg. 1: 0 = images of Q (minimal sets; supersets of
+    earlier levels removed), 1 = preimages of singletons (maximal sets;
+    subsets of earlier levels removed)."""
+    d, n, k = _delta(delta)
+    sizes = np.zeros(depth + 1, np.int64)
+    rc = _load().oracle_reduced_level_sizes(n, k, _ptr(d), direction, depth, max_sets, _ptr(sizes))
+    if rc:
+        raise OracleError(rc, "oracle_reduced_level_sizes")
+    return sizes.tolist()
+
+
+def bidir_reduced(delta, fwd_depth: int = -1, max_sets: int = 50_000_000, word_cap: int = 1 << 20):
+    """O3: (r, word, fwd_sizes, bwd_sizes) by Alg. 1 with the inclusion
+    reductions.  fwd_depth >= 0 fixes the forward depth of the meet (the
+    word depends on it; r and the sizes do not)."""
+    d, n, k = _delta(delta)
+    r = np.zeros(1, np.int32)
+    w = np.zeros(word_cap, np.uint8)
+    cap = 4096
+    fs = np.zeros(cap, np.int64)
+    bs = np.zeros(cap, np.int64)
+    nf = np.zeros(1, np.int32)
+    nb = np.zeros(1, np.int32)
+    rc = _load().oracle_bidir_reduced(n, k, _ptr(d), max_sets, fwd_depth, _ptr(r), _ptr(w), word_cap, _ptr(fs),
+                                      _ptr(nf), _ptr(bs), _ptr(nb), cap)
+    if rc:
+        raise OracleError(rc, "oracle_bidir_reduced")
     return int(r[0]), w[: r[0]].tolist(), fs[: nf[0]].tolist(), bs[: nb[0]].tolist()
 
 

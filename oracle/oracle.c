@@ -30,6 +30,13 @@
  *                          history; the meet condition X subset of Y
  *                          (Section 2, the meet of the two searches) checked
  *                          by brute force after every step.
+ *   oracle_reduced_level_sizes, oracle_bidir_reduced
+ *                          Alg. 1 with its inclusion reductions (Section
+ *                          2.1): duplicates removed, then the sets that are
+ *                          not minimal (BFS) / maximal (IBFS) in their list
+ *                          (MarkProperSupersets), then the supersets (BFS) /
+ *                          subsets (IBFS) of every set of an earlier level
+ *                          (the history); all by brute force over pairs.
  *   oracle_is_synchronizing  Section 2, first step: every pair of states can
  *                          be mapped to one state.
  *
@@ -560,6 +567,189 @@ int oracle_bidir(int n, int k, const int32_t *delta, int64_t max_sets, int32_t *
     }
     for (int d = 0; d < cap; d++) { level_free(&F[d]); level_free(&B[d]); }
     free(F); free(B); free(HF.sets); free(HB.sets);
+    return rc;
+}
+
+/* ------------------------------------------------------------------ */
+/* O3: Alg. 1 with the inclusion reductions (Section 2.1)              */
+/* ------------------------------------------------------------------ */
+
+/* X subset of Y, word by word (the same relation as set_subset). */
+static int subset_words(const uint64_t *x, const uint64_t *y, int W) {
+    for (int w = 0; w < W; w++)
+        if (x[w] & ~y[w]) return 0;
+    return 1;
+}
+
+/*
+ * One BFS (dir = 0) or IBFS (dir = 1) iteration with the list reductions of
+ * Alg. 1, in the paper's order:
+ *   1. CalculateImages / CalculatePreimages (empty preimages dropped);
+ *   2. delete duplicates (lexicographic sort; of every set the candidate
+ *      with the smallest id p*k + a stays);
+ *   3. delete the sets that are not minimal (BFS) / not maximal (IBFS)
+ *      with respect to inclusion among the sets of the list
+ *      (MarkProperSupersets): every pair is checked;
+ *   4. delete the supersets (BFS) / subsets (IBFS) of every set kept at an
+ *      earlier level of the same direction (MarkSupersets against the
+ *      history H = the union of those levels): every pair is checked.
+ * Steps 3 and 4 both test the list as it stands after step 2, so the order
+ * in which sets are removed does not matter.  The kept sets leave in
+ * candidate-id order (parent position, then letter).  hist: the kept
+ * levels 0..nh-1 of this direction.
+ */
+static int expand_reduced(int n, int k, const int32_t *delta, int dir, const level_t *L,
+                          const level_t *hist, int nh, level_t *out, int64_t max_sets) {
+    int W = words_for(n);
+    int64_t m = L->count * (int64_t)k;
+    if (m > max_sets) return OR_ETOOBIG;
+    uint64_t *cand = (uint64_t *)malloc((size_t)(m ? m : 1) * W * sizeof(uint64_t));
+    int64_t *ids = (int64_t *)malloc((size_t)(m ? m : 1) * sizeof(int64_t));
+    uint8_t *keep = (uint8_t *)calloc((size_t)(m ? m : 1), 1);
+    if (!cand || !ids || !keep) {
+        free(cand); free(ids); free(keep);
+        return OR_ENOMEM;
+    }
+    int64_t nvalid = 0;
+    for (int64_t p = 0; p < L->count; p++) {
+        for (int a = 0; a < k; a++) {
+            int64_t id = p * k + a;
+            uint64_t *T = cand + id * W;
+            if (dir == 0) set_image(n, delta + (size_t)a * n, L->sets + p * W, T, W);
+            else set_preimage(n, delta + (size_t)a * n, L->sets + p * W, T, W);
+            if (dir == 1 && set_first(T, n) < 0) continue; /* empty preimage */
+            ids[nvalid++] = id;
+        }
+    }
+    int rc = sort_ids(ids, nvalid, cand, n, W);
+    if (rc) { free(cand); free(ids); free(keep); return rc; }
+    /* 2. the first of every run of equal sets */
+    int64_t u = 0;
+    for (int64_t i = 0; i < nvalid; i++) {
+        if (i > 0 && set_cmp(cand + ids[i - 1] * W, cand + ids[i] * W, n) == 0) continue;
+        ids[u++] = ids[i];
+    }
+    uint8_t *gone = (uint8_t *)calloc((size_t)(u ? u : 1), 1);
+    if (!gone) { free(cand); free(ids); free(keep); return OR_ENOMEM; }
+    /* 3. self-reduction: the sets are distinct, so inclusion is proper */
+    for (int64_t a = 0; a < u; a++) {
+        const uint64_t *X = cand + ids[a] * W;
+        for (int64_t b = 0; b < u && !gone[a]; b++) {
+            if (b == a) continue;
+            const uint64_t *Y = cand + ids[b] * W;
+            if (dir == 0 ? subset_words(Y, X, W) : subset_words(X, Y, W)) gone[a] = 1;
+        }
+    }
+    /* 4. reduction by the history */
+    for (int64_t a = 0; a < u; a++) {
+        const uint64_t *X = cand + ids[a] * W;
+        for (int h = 0; h < nh && !gone[a]; h++)
+            for (int64_t z = 0; z < hist[h].count && !gone[a]; z++) {
+                const uint64_t *Z = hist[h].sets + z * W;
+                if (dir == 0 ? subset_words(Z, X, W) : subset_words(X, Z, W)) gone[a] = 1;
+            }
+    }
+    int64_t nkept = 0;
+    for (int64_t a = 0; a < u; a++)
+        if (!gone[a]) { keep[ids[a]] = 1; nkept++; }
+    out->count = 0;
+    rc = level_reserve(out, nkept ? nkept : 1, W);
+    for (int64_t id = 0; !rc && id < m; id++)
+        if (keep[id]) rc = level_push(out, cand + id * W, id / k, (int)(id % k), W);
+    free(gone); free(cand); free(ids); free(keep);
+    return rc;
+}
+
+/* Sizes of the reduced levels 0..depth of one direction: dir 0 = images of
+ * Q (minimal sets, supersets of earlier levels removed), 1 = preimages of
+ * the singletons (maximal sets, subsets of earlier levels removed). */
+int oracle_reduced_level_sizes(int n, int k, const int32_t *delta, int dir, int32_t depth,
+                               int64_t max_sets, int64_t *sizes) {
+    int rc = check_automaton(n, k, delta);
+    if (rc) return rc;
+    if ((dir != 0 && dir != 1) || depth < 0 || !sizes || n > 1024) return OR_EINVAL;
+    int W = words_for(n);
+    level_t *lv = (level_t *)calloc((size_t)depth + 1, sizeof(level_t));
+    if (!lv) return OR_ENOMEM;
+    if (dir == 0) level_root_Q(&lv[0], n, W);
+    else rc = level_root_singletons(&lv[0], n, W);
+    int64_t stored = lv[0].count;
+    if (!rc) sizes[0] = lv[0].count;
+    for (int d = 1; !rc && d <= depth; d++) {
+        rc = expand_reduced(n, k, delta, dir, &lv[d - 1], lv, d, &lv[d], max_sets - stored);
+        if (rc) break;
+        stored += lv[d].count;
+        if (stored > max_sets) { rc = OR_ETOOBIG; break; }
+        sizes[d] = lv[d].count;
+    }
+    for (int d = 0; d <= depth; d++) level_free(&lv[d]);
+    free(lv);
+    return rc;
+}
+
+/*
+ * Alg. 1 with the inclusion reductions.  The reduced levels of each side
+ * depend on that side alone, and the searches first meet when the depths
+ * add up to r whatever the order of the steps; the word does depend on the
+ * split.  fwd_depth < 0: the side with fewer sets steps (equal sizes step
+ * forward); fwd_depth >= 0: forward steps until the forward depth is
+ * fwd_depth, then backward steps (so the first meet is at i = fwd_depth
+ * when fwd_depth <= r).  The word is the parent chain of the first meeting
+ * forward set in list order followed by the least suffix (least_suffix).
+ */
+int oracle_bidir_reduced(int n, int k, const int32_t *delta, int64_t max_sets, int32_t fwd_depth,
+                         int32_t *r_out, uint8_t *word, int32_t word_cap, int64_t *fsizes, int32_t *nf,
+                         int64_t *bsizes, int32_t *nb, int32_t sizes_cap) {
+    int rc = check_automaton(n, k, delta);
+    if (rc) return rc;
+    if (!r_out || n > 1024) return OR_EINVAL;
+    int W = words_for(n);
+    int cap = 4096; /* levels per direction */
+    level_t *F = (level_t *)calloc((size_t)cap, sizeof(level_t));
+    level_t *B = (level_t *)calloc((size_t)cap, sizeof(level_t));
+    if (!F || !B) { free(F); free(B); return OR_ENOMEM; }
+    int i = 0, j = 0;
+    level_root_Q(&F[0], n, W);
+    rc = level_root_singletons(&B[0], n, W);
+    int64_t stored = F[0].count + B[0].count;
+    int64_t hit = rc ? -1 : first_meet(&F[0], &B[0], n, W);
+    while (!rc && hit < 0) {
+        if (i + 1 >= cap || j + 1 >= cap) { rc = OR_ETOOBIG; break; }
+        int dir = fwd_depth >= 0 ? (i < fwd_depth ? 0 : 1) : (F[i].count <= B[j].count ? 0 : 1);
+        if (dir == 0) {
+            rc = expand_reduced(n, k, delta, 0, &F[i], F, i + 1, &F[i + 1], max_sets - stored);
+            if (rc) break;
+            i++;
+            stored += F[i].count;
+            if (F[i].count == 0) { rc = OR_ENOTSYNC; break; }
+        } else {
+            rc = expand_reduced(n, k, delta, 1, &B[j], B, j + 1, &B[j + 1], max_sets - stored);
+            if (rc) break;
+            j++;
+            stored += B[j].count;
+            if (B[j].count == 0) { rc = OR_ENOTSYNC; break; }
+        }
+        if (stored > max_sets) { rc = OR_ETOOBIG; break; }
+        hit = first_meet(&F[i], &B[j], n, W);
+    }
+    if (!rc) {
+        int r = i + j;
+        *r_out = r;
+        if (nf) *nf = i + 1;
+        if (nb) *nb = j + 1;
+        for (int d = 0; fsizes && d <= i && d < sizes_cap; d++) fsizes[d] = F[d].count;
+        for (int d = 0; bsizes && d <= j && d < sizes_cap; d++) bsizes[d] = B[d].count;
+        if (word) {
+            if (r <= word_cap) {
+                chain_word(F, i, hit, word);
+                rc = least_suffix(n, k, delta, F[i].sets + hit * W, j, max_sets, word + i);
+            } else {
+                rc = OR_EWORDCAP;
+            }
+        }
+    }
+    for (int d = 0; d < cap; d++) { level_free(&F[d]); level_free(&B[d]); }
+    free(F); free(B);
     return rc;
 }
 

@@ -216,3 +216,135 @@ def test_rejects_bad_input():
     with pytest.raises(oracle.OracleError):
         oracle.forward(np.array([[0, 5]], dtype=np.int32))
     assert not oracle.is_synchronizing(np.array([[1, 0], [0, 1]], dtype=np.int32))
+
+
+# ---------------------------------------------------------------- inclusion reductions (Alg. 1)
+
+def reachable_by_depth(delta, direction, depth):
+    """R[i] = the sets reachable at depth exactly i, from the definition:
+    forward {delta(Q, w) : |w| = i}; backward the nonempty
+    {delta^{-1}({q}, y) : |y| = i}.  Plain Python word enumeration."""
+    delta = [list(map(int, row)) for row in np.asarray(delta)]
+    k, n = len(delta), len(delta[0])
+    out = []
+    for d in range(depth + 1):
+        cur = set()
+        for w in itertools.product(range(k), repeat=d):
+            if direction == 0:
+                s = set(range(n))
+                for a in w:
+                    s = {delta[a][q] for q in s}
+                cur.add(frozenset(s))
+            else:
+                for q in range(n):
+                    s = {q}
+                    for a in reversed(w):
+                        s = {p for p in range(n) if delta[a][p] in s}
+                    if s:
+                        cur.add(frozenset(s))
+        out.append(cur)
+    return out
+
+
+def reduced_levels_by_definition(delta, direction, depth):
+    """The reduced level i, characterised without the search's recursion:
+    forward, the sets S reachable at depth i with no set reachable at depth
+    i that is a proper subset of S and no set reachable at a smaller depth
+    that is a subset of S; backward, the same with supersets.  (A reachable
+    set that the reduced search drops always has a kept subset -- superset
+    backward -- at the same or a smaller depth, because images and
+    preimages are monotone under inclusion; so the kept sets are exactly
+    these.)"""
+    R = reachable_by_depth(delta, direction, depth)
+    below = lambda a, b: a <= b if direction == 0 else a >= b  # noqa: E731  a "beats" b
+    levels = []
+    earlier = set()
+    for i in range(depth + 1):
+        keep = set()
+        for S in R[i]:
+            if any(below(T, S) for T in earlier):
+                continue
+            if any(T != S and below(T, S) for T in R[i]):
+                continue
+            keep.add(S)
+        levels.append(keep)
+        earlier |= R[i]
+    return levels
+
+
+@pytest.mark.parametrize("d", _small_random(14, (2, 6), (1, 3), 61))
+def test_reduced_level_sizes_equal_definition(d):
+    depth = 5
+    for direction in (0, 1):
+        want = [len(L) for L in reduced_levels_by_definition(d, direction, depth)]
+        assert oracle.reduced_level_sizes(d, direction, depth) == want
+
+
+def test_reduced_level_sizes_all_binary_n3():
+    for flat in itertools.product(range(3), repeat=6):
+        d = np.array(flat, dtype=np.int32).reshape(2, 3)
+        for direction in (0, 1):
+            want = [len(L) for L in reduced_levels_by_definition(d, direction, 4)]
+            assert oracle.reduced_level_sizes(d, direction, 4) == want
+
+
+def reduced_word_by_definition(delta, r, i):
+    """The reduced search's word for the split (i, r - i), by enumeration:
+    x = the lexicographically least word of length i all of whose prefixes
+    (x itself included) reach a kept set of their depth and whose set lies
+    inside some kept backward set of depth r - i; then the least y of
+    length r - i with |delta(delta(Q, x), y)| = 1."""
+    dl = [list(map(int, row)) for row in np.asarray(delta)]
+    k, n = len(dl), len(dl[0])
+    j = r - i
+    F = reduced_levels_by_definition(delta, 0, i)
+    B = reduced_levels_by_definition(delta, 1, j)[j]
+    for x in itertools.product(range(k), repeat=i):
+        s = frozenset(range(n))
+        ok = s in F[0]
+        for t, a in enumerate(x):
+            s = frozenset(dl[a][q] for q in s)
+            ok = ok and s in F[t + 1]
+        if ok and any(s <= Y for Y in B):
+            for y in itertools.product(range(k), repeat=j):
+                u = set(s)
+                for a in y:
+                    u = {dl[a][q] for q in u}
+                if len(u) == 1:
+                    return list(x) + list(y)
+    raise AssertionError("no reduced word")
+
+
+@pytest.mark.parametrize("d", _small_random(16, (3, 7), (2, 3), 71))
+def test_reduced_search_r_word_and_sizes(d):
+    rb, wb = oracle.brute(d, 16)
+    r, w, fs, bs = oracle.bidir_reduced(d)
+    assert r == rb and len(w) == r and resets(d, w)
+    assert fs == [len(L) for L in reduced_levels_by_definition(d, 0, len(fs) - 1)]
+    assert bs == [len(L) for L in reduced_levels_by_definition(d, 1, len(bs) - 1)]
+    assert len(fs) + len(bs) - 2 == r
+    assert w == reduced_word_by_definition(d, r, len(fs) - 1)
+    for i in range(r + 1):  # every split: same r, the word of that split
+        ri, wi, fi, bi = oracle.bidir_reduced(d, fwd_depth=i)
+        assert ri == r and len(fi) - 1 == i and len(bi) - 1 == r - i
+        assert wi == reduced_word_by_definition(d, r, i)
+    # a split with no forward step gives the least reset word of all
+    assert oracle.bidir_reduced(d, fwd_depth=0)[1] == wb
+
+
+@pytest.mark.parametrize("n", [2, 3, 5, 8, 12])
+def test_reduced_cerny_closed_form(n):
+    d = gen.cerny(n)
+    r, w, _, _ = oracle.bidir_reduced(d)
+    assert r == (n - 1) ** 2 and resets(d, w)
+    assert oracle.bidir_reduced(d, fwd_depth=0)[1] == cerny_word(n)
+
+
+@pytest.mark.parametrize("d", _small_random(10, (20, 40), (2, 3), 83))
+def test_reduced_r_equals_unreduced(d):
+    r, _, _, _ = oracle.bidir(d)
+    rr, wr, fs, bs = oracle.bidir_reduced(d)
+    assert rr == r and resets(d, wr)
+    full_f = oracle.level_sizes(d, 0, len(fs) - 1)
+    full_b = oracle.level_sizes(d, 1, len(bs) - 1)
+    assert all(a <= b for a, b in zip(fs, full_f)) and all(a <= b for a, b in zip(bs, full_b))
