@@ -57,6 +57,8 @@ def _load():
         lib.oracle_is_synchronizing.argtypes = [ctypes.c_int, ctypes.c_int, p]
         lib.oracle_reduced_level_sizes.argtypes = [ctypes.c_int, ctypes.c_int, p, ctypes.c_int, i32, i64, p]
         lib.oracle_bidir_reduced.argtypes = [ctypes.c_int, ctypes.c_int, p, i64, i32, p, p, i32, p, p, p, p, i32]
+        lib.oracle_beam.argtypes = [ctypes.c_int, ctypes.c_int, p, i64, i32, p, p, i32, p, i32, p]
+        lib.oracle_beam.restype = ctypes.c_int
         for f in (lib.oracle_brute, lib.oracle_forward, lib.oracle_level_sizes, lib.oracle_bidir,
                   lib.oracle_is_synchronizing, lib.oracle_reduced_level_sizes, lib.oracle_bidir_reduced):
             f.restype = ctypes.c_int
@@ -159,6 +161,21 @@ def bidir_reduced(delta, fwd_depth: int = -1, max_sets: int = 50_000_000, word_c
     if rc:
         raise OracleError(rc, "oracle_bidir_reduced")
     return int(r[0]), w[: r[0]].tolist(), fs[: nf[0]].tolist(), bs[: nb[0]].tolist()
+
+
+def beam(delta, beam_size: int, max_depth: int = 1 << 16):
+    """O4: (R, word, level_sizes) of the cut-off inverse BFS that keeps the
+    beam_size largest preimages of every depth; R >= r."""
+    d, n, k = _delta(delta)
+    r = np.zeros(1, np.int32)
+    w = np.zeros(max_depth + 1, np.uint8)
+    sizes = np.zeros(max_depth + 1, np.int64)
+    nl = np.zeros(1, np.int32)
+    rc = _load().oracle_beam(n, k, _ptr(d), beam_size, max_depth, _ptr(r), _ptr(w), len(w), _ptr(sizes), len(sizes),
+                             _ptr(nl))
+    if rc:
+        raise OracleError(rc, "oracle_beam")
+    return int(r[0]), w[: r[0]].tolist(), sizes[: nl[0]].tolist()
 
 
 def is_synchronizing(delta) -> bool:

@@ -37,6 +37,10 @@
  *                          (MarkProperSupersets), then the supersets (BFS) /
  *                          subsets (IBFS) of every set of an earlier level
  *                          (the history); all by brute force over pairs.
+ *   oracle_beam            Section 2.1.3: the heuristic upper bound R from
+ *                          an inverse BFS that keeps only the `beam`
+ *                          largest preimages of every depth (the cut-off
+ *                          inverse BFS the paper cites).
  *   oracle_is_synchronizing  Section 2, first step: every pair of states can
  *                          be mapped to one state.
  *
@@ -750,6 +754,116 @@ int oracle_bidir_reduced(int n, int k, const int32_t *delta, int64_t max_sets, i
     }
     for (int d = 0; d < cap; d++) { level_free(&F[d]); level_free(&B[d]); }
     free(F); free(B);
+    return rc;
+}
+
+/* ------------------------------------------------------------------ */
+/* O4: beam upper bound, inverse BFS with a cut-off (Section 2.1.3)    */
+/* ------------------------------------------------------------------ */
+
+typedef struct {
+    const uint64_t *cand;
+    int n, W;
+} beam_ctx_t;
+
+/* Order of the beam's cut: larger sets first, then smaller candidate id. */
+static int beam_before(const beam_ctx_t *c, int64_t a, int64_t b) {
+    int ca = set_size(c->cand + a * c->W, c->n), cb = set_size(c->cand + b * c->W, c->n);
+    if (ca != cb) return ca > cb;
+    return a < b;
+}
+
+/*
+ * The beam search that gives the paper's upper bound R (Section 2.1.3, the
+ * cut-off inverse BFS it cites): level 0 is the n singletons; level d + 1
+ * is made of the preimages delta^{-1}(S, a) of the sets S of level d under
+ * every letter a, empty ones dropped and duplicates removed (the smallest
+ * candidate id p*k + a of every set stays), of which only the `beam`
+ * largest are kept (ties: smaller candidate id first), in candidate-id
+ * order.  No history is kept.  The first depth R at which Q itself is a
+ * kept set gives the reset word y with delta^{-1}({q}, y) = Q, i.e.
+ * delta(Q, y) = {q}: the letters on the chain from that set back to its
+ * singleton, last-applied first.  Kept sizes go to sizes[0..R].
+ * Returns OR_ENOTFOUND when no level up to max_depth holds Q.
+ */
+int oracle_beam(int n, int k, const int32_t *delta, int64_t beam, int32_t max_depth, int32_t *R_out,
+                uint8_t *word, int32_t word_cap, int64_t *sizes, int32_t sizes_cap, int32_t *nlevels) {
+    int rc = check_automaton(n, k, delta);
+    if (rc) return rc;
+    if (!R_out || beam < 1 || max_depth < 0 || n > 8192) return OR_EINVAL;
+    int W = words_for(n);
+    int cap = max_depth + 1;
+    level_t *lv = (level_t *)calloc((size_t)cap, sizeof(level_t));
+    if (!lv) return OR_ENOMEM;
+    rc = level_root_singletons(&lv[0], n, W);
+    int64_t hit = (n == 1) ? 0 : -1;
+    int depth = 0;
+    while (!rc && hit < 0) {
+        if (depth == max_depth) { rc = OR_ENOTFOUND; break; }
+        const level_t *L = &lv[depth];
+        int64_t m = L->count * (int64_t)k;
+        uint64_t *cand = (uint64_t *)malloc((size_t)(m ? m : 1) * W * sizeof(uint64_t));
+        int64_t *ids = (int64_t *)malloc((size_t)(m ? m : 1) * sizeof(int64_t));
+        uint8_t *keep = (uint8_t *)calloc((size_t)(m ? m : 1), 1);
+        if (!cand || !ids || !keep) { free(cand); free(ids); free(keep); rc = OR_ENOMEM; break; }
+        int64_t nvalid = 0;
+        for (int64_t p = 0; p < L->count; p++)
+            for (int a = 0; a < k; a++) {
+                int64_t id = p * k + a;
+                set_preimage(n, delta + (size_t)a * n, L->sets + p * W, cand + id * W, W);
+                if (set_first(cand + id * W, n) >= 0) ids[nvalid++] = id;
+            }
+        rc = sort_ids(ids, nvalid, cand, n, W);
+        int64_t u = 0;
+        for (int64_t i = 0; !rc && i < nvalid; i++) {
+            if (i > 0 && set_cmp(cand + ids[i - 1] * W, cand + ids[i] * W, n) == 0) continue;
+            ids[u++] = ids[i];
+        }
+        /* the cut: insertion sort would be quadratic; a plain merge sort by
+         * (size descending, id ascending) */
+        beam_ctx_t ctx = {cand, n, W};
+        int64_t *tmp = (int64_t *)malloc((size_t)(u ? u : 1) * sizeof(int64_t));
+        if (!rc && !tmp) rc = OR_ENOMEM;
+        for (int64_t width = 1; !rc && width < u; width *= 2) {
+            for (int64_t lo = 0; lo < u; lo += 2 * width) {
+                int64_t mid = lo + width < u ? lo + width : u, hi = lo + 2 * width < u ? lo + 2 * width : u;
+                int64_t i = lo, j = mid, o = lo;
+                while (i < mid && j < hi) tmp[o++] = beam_before(&ctx, ids[j], ids[i]) ? ids[j++] : ids[i++];
+                while (i < mid) tmp[o++] = ids[i++];
+                while (j < hi) tmp[o++] = ids[j++];
+            }
+            memcpy(ids, tmp, (size_t)u * sizeof(int64_t));
+        }
+        free(tmp);
+        int64_t kept = u < beam ? u : beam;
+        for (int64_t i = 0; !rc && i < kept; i++) keep[ids[i]] = 1;
+        if (!rc) rc = level_reserve(&lv[depth + 1], kept ? kept : 1, W);
+        for (int64_t id = 0; !rc && id < m; id++)
+            if (keep[id]) rc = level_push(&lv[depth + 1], cand + id * W, id / k, (int)(id % k), W);
+        free(cand); free(ids); free(keep);
+        if (rc) break;
+        depth++;
+        if (lv[depth].count == 0) { rc = OR_ENOTSYNC; break; }
+        for (int64_t i = 0; i < lv[depth].count && hit < 0; i++)
+            if (set_size(lv[depth].sets + i * W, n) == n) hit = i;
+    }
+    if (!rc) {
+        *R_out = depth;
+        if (nlevels) *nlevels = depth + 1;
+        for (int d = 0; sizes && d <= depth && d < sizes_cap; d++) sizes[d] = lv[d].count;
+        if (word) {
+            if (depth > word_cap) rc = OR_EWORDCAP;
+            else {
+                int64_t pos = hit;
+                for (int d = depth; d > 0; d--) { /* the set of depth d was made by the (depth - d + 1)-th letter */
+                    word[depth - d] = lv[d].letter[pos];
+                    pos = lv[d].parent[pos];
+                }
+            }
+        }
+    }
+    for (int d = 0; d < cap; d++) level_free(&lv[d]);
+    free(lv);
     return rc;
 }
 

@@ -348,3 +348,58 @@ def test_reduced_r_equals_unreduced(d):
     full_f = oracle.level_sizes(d, 0, len(fs) - 1)
     full_b = oracle.level_sizes(d, 1, len(bs) - 1)
     assert all(a <= b for a, b in zip(fs, full_f)) and all(a <= b for a, b in zip(bs, full_b))
+
+
+# ---------------------------------------------------------------- beam upper bound (Section 2.1.3)
+
+def beam_by_definition(delta, B, max_depth):
+    """The cut-off inverse BFS in plain Python: level 0 = the singletons in
+    order; each level = the distinct nonempty preimages of the previous
+    level's sets in candidate order (parent position, then letter), of
+    which the B largest are kept (ties: earlier candidate first), in
+    candidate order; returns (R, sizes) for the first level holding Q."""
+    dl = [list(map(int, row)) for row in np.asarray(delta)]
+    k, n = len(dl), len(dl[0])
+    cur = [frozenset([q]) for q in range(n)]
+    sizes = [len(cur)]
+    if n == 1:
+        return 0, sizes
+    for depth in range(1, max_depth + 1):
+        seen, cands = set(), []
+        for S in cur:
+            for a in range(k):
+                T = frozenset(p for p in range(n) if dl[a][p] in S)
+                if T and T not in seen:
+                    seen.add(T)
+                    cands.append(T)
+        order = sorted(range(len(cands)), key=lambda i: (-len(cands[i]), i))[:B]
+        cur = [cands[i] for i in sorted(order)]
+        sizes.append(len(cur))
+        if any(len(S) == n for S in cur):
+            return depth, sizes
+    return None, sizes
+
+
+@pytest.mark.parametrize("d", _small_random(20, (3, 9), (2, 3), 91))
+def test_beam_equals_definition_and_bounds_r(d):
+    r = oracle.brute(d, 20)[0]
+    for B in (2, 3, 5, 1 << 30):
+        want_R, want_sizes = beam_by_definition(d, B, 40)
+        if want_R is None:
+            with pytest.raises(oracle.OracleError):
+                oracle.beam(d, B, max_depth=40)
+            continue
+        R, w, sizes = oracle.beam(d, B, max_depth=40)
+        assert (R, sizes) == (want_R, want_sizes)
+        assert len(w) == R and resets(d, w) and R >= r
+        if B == 1 << 30:  # no cut: the inverse BFS reaches Q first at depth r
+            assert R == r
+
+
+@pytest.mark.parametrize("n", [2, 4, 7, 10])
+def test_beam_cerny(n):
+    d = gen.cerny(n)
+    R, w, _ = oracle.beam(d, 1 << 30)
+    assert R == (n - 1) ** 2 and resets(d, w)
+    R1, w1, sizes = oracle.beam(d, 1)  # a beam of one still finds a word here
+    assert R1 >= (n - 1) ** 2 and resets(d, w1) and max(sizes[1:] or [1]) == 1
