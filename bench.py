@@ -22,9 +22,10 @@ least shortest reset word of every instance.
                 instances/s, admissions while other searches ran.
   one_at_a_time sw_reset_threshold in a loop over a sample, and the batched
                 call on the same sample.
-  cpu_baseline  the CPU oracle (bidirectional) on a fixed stratified sample
-                of the workload, every instance run to completion: all cores
-                and single-threaded.
+  cpu_baseline  the CPU oracle (bidirectional) on a fixed sample of the
+                workload's stratum n <= 100 (--cpu-full: of the whole
+                workload), every instance run to completion: all cores and
+                single-threaded.
 
 --workload hard300 / hard400 (/ hard500 / hard570): one hard random
 automaton (seed 0) searched alone, with r, time, peak sets, pairs/s, and the
@@ -60,11 +61,11 @@ SM_MAX_MHZ_FALLBACK = 2070.0
 N_SMS_NOMINAL = 152
 # DRAM bytes (read + write) of the meet kernel per backward row it
 # transposes, from an ncu capture (dram__bytes_read.sum +
-# dram__bytes_write.sum) of every meet launch of two steps of the first 512
-# automata of this workload; the full workload is too large for a
-# multi-pass capture, so its traffic per launch is this figure times the
-# rows one launch transposes.
-MEET_DRAM_BYTES_PER_ROW = 14.2
+# dram__bytes_write.sum) of single meet launches of the first 512 automata
+# of this workload; the full workload is too large for a multi-pass
+# capture, so its traffic per launch is this figure times the rows one
+# launch transposes.  None until captured for the current kernel.
+MEET_DRAM_BYTES_PER_ROW = None
 
 
 def rank_seeds(rank: int, count: int) -> range:
@@ -93,6 +94,11 @@ def workload(name: str, rank: int = 0):
                                                   "instances": 1}
     if name == "cerny":
         return [gen.cerny(n) for n in range(16, 29)], {"workload": "Cerny automata n=16..28", "instances": 13}
+    if name in ("beam1000", "beam2000", "beam5000"):
+        n = int(name[4:])
+        return [gen.random_automaton(n, 2, 0)], {
+            "workload": f"beam upper bound: random binary automaton n={n} k=2 seed 0, beam n*ceil(log2 n) = "
+                        f"{n * int(np.ceil(np.log2(n)))}, {(n + 63) // 64}x64-bit bitsets", "instances": 1}
     if name in ("hard300", "hard400", "hard500", "hard570"):
         n = int(name[4:])
         return [gen.random_automaton(n, 2, 0)], {
@@ -230,18 +236,24 @@ def run_reference(args, ds, cfg, rank, world):
     print(json.dumps(line), flush=True)
 
 
-def cpu_baseline_line(ds, m: int, cores: int):
-    """The oracle on a fixed stratified sample of the workload (m instances,
-    seeds spread evenly), every instance run to completion: all cores (one
-    process per core) and single-threaded (the summed per-instance CPU
-    times)."""
-    idx = stratified_seeds(len(ds), m)
+def cpu_baseline_line(ds, m: int, cores: int, n_max: int = 0):
+    """The oracle on a fixed sample of the workload, every instance run to
+    completion: all cores (one process per core) and single-threaded (the
+    summed per-instance CPU times).  n_max = 0: m instances at evenly spread
+    seeds of the whole workload (unbiased, but its hardest instances take
+    minutes each on one core); n_max > 0: m instances evenly spread over the
+    stratum n <= n_max (bounded, and stated as such)."""
+    pool_idx = [i for i in range(len(ds)) if n_max <= 0 or ds[i].shape[1] <= n_max]
+    m = min(m, len(pool_idx))
+    idx = [pool_idx[j] for j in stratified_seeds(len(pool_idx), m)]
     with oracle_pool(min(cores, m)) as pool:
         wall, cpu_s, rs = cpu_fixed_sample(pool, [ds[i] for i in idx])
+    where = (f"the stratum n <= {n_max} ({len(pool_idx)} of {len(ds)} instances)" if n_max > 0
+             else "the whole workload")
     return {"value": m / wall, "unit": "instances/s", "cores": min(cores, m), "kind": "oracle",
             "single_thread": m / cpu_s if cpu_s else 0.0,
-            "sample": f"{m} instances at seeds {idx[0]}, {idx[1]}, ... {idx[-1]} (every {len(ds) // m}th), "
-                      f"each run to completion by the bidirectional oracle; wall {wall:.1f} s on "
+            "sample": f"{m} instances evenly spread over {where}, indices {idx[0]}, {idx[1] if m > 1 else ''}, ... "
+                      f"{idx[-1]}, each run to completion by the bidirectional oracle; wall {wall:.1f} s on "
                       f"{min(cores, m)} processes, {cpu_s:.1f} s of summed CPU time"}
 
 
@@ -326,10 +338,14 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="c3",
-                    choices=["c3", "c1", "cerny", "hard300", "hard400", "hard500", "hard570"])
+                    choices=["c3", "c1", "cerny", "hard300", "hard400", "hard500", "hard570", "beam1000", "beam2000",
+                             "beam5000"])
     ap.add_argument("--ws-gb", type=float, default=160.0)
-    ap.add_argument("--cpu-sample", type=int, default=16,
-                    help="instances of the fixed stratified sample the CPU oracle runs to completion")
+    ap.add_argument("--cpu-sample", type=int, default=32,
+                    help="instances of the fixed sample the CPU oracle runs to completion")
+    ap.add_argument("--cpu-full", action="store_true",
+                    help="CPU sample spread over the whole workload instead of the stratum n <= --ref-n-max "
+                         "(unbiased; several minutes on the heavy-tailed instances)")
     ap.add_argument("--ref-n-max", type=int, default=100,
                     help="reference arm: the stratum (n <= this) its steps draw instances from")
     ap.add_argument("--one-sample", type=int, default=256)
@@ -353,8 +369,12 @@ def main():
     cfg["l2"] = "flushed between steps (256 MiB write)"
     cfg["parallelism"] = f"replicas x{world} (independent instances per GPU)"
 
-    hard = args.workload.startswith("hard")
+    hard = args.workload.startswith("hard") or args.workload.startswith("beam")
     if args.impl == "reference":
+        if args.workload.startswith("beam"):
+            if rank == 0:
+                run_reference_beam(args, ds[0], cfg)
+            return
         if hard:
             if rank == 0:
                 print(json.dumps({"impl": "reference", "unavailable": "the CPU oracle does not finish a random "
@@ -366,7 +386,8 @@ def main():
     # CPU baseline first: its process pool is spawned before any CUDA work
     cpu = None
     if rank == 0 and not args.no_cpu and not hard:
-        cpu = cpu_baseline_line(ds, min(args.cpu_sample, len(ds)), os.cpu_count() or 1)
+        cpu = cpu_baseline_line(ds, min(args.cpu_sample, len(ds)), os.cpu_count() or 1,
+                                0 if args.cpu_full else args.ref_n_max)
 
     import torch
     import torch.distributed as dist
@@ -395,9 +416,17 @@ def main():
         cfg["options"] = "library defaults"
     props = torch.cuda.get_device_properties(local)
     nsm = props.multi_processor_count
+    lop3_probe = sw.sw_probe_int_peak()  # LOP3 per SM clock, measured
     peak = INT32_LANES_PER_SM * nsm * SM_MAX_MHZ_FALLBACK * 1e6 / 1e12
     smem_peak = SMEM_BYTES_PER_CLK_SM * nsm * SM_MAX_MHZ_FALLBACK * 1e6 / 1e12
     hbm_peak = hbm_peak_gbs()
+    if args.workload.startswith("beam"):
+        line = run_beam(args, ds[0], cfg, sw, torch, local, world)
+        if rank == 0:
+            print(json.dumps(line), flush=True)
+        if world > 1:
+            dist.destroy_process_group()
+        return
     if hard:
         line = run_hard(args, ds[0], cfg, sw, torch, local, world, peak, nsm)
         if rank == 0:
@@ -537,10 +566,14 @@ def main():
                      "pairs_per_step": pairs, "pairs_per_sec_in_kernel": pairs / sec if sec > 0 else 0.0,
                      "launches_per_step": launches, "avg_launch_ms": meet_ms / max(launches, 1),
                      "peak_basis": f"{INT32_LANES_PER_SM} int32 lanes/SM x {nsm} SMs x "
-                                   f"{SM_MAX_MHZ_FALLBACK:.0f} MHz (max SM clock)"},
+                                   f"{SM_MAX_MHZ_FALLBACK:.0f} MHz (max SM clock); a LOP3 probe measured "
+                                   f"{lop3_probe:.1f} per SM clock (sw_probe_int_peak)",
+                     "lop3_probe_per_clk_per_sm": lop3_probe},
         "roofline_hbm": hbm,
+        "roofline_mark": mark_roofline(stats, lw, W, peak),
         "subset_checks_per_sec": pairs / (ms * 1e-3),
         "kernel_ms_per_step": {"meet": meet_ms, "expand": expand_ms, "compact": compact_ms,
+                               "mark": sum(s["mark_ms"] for s in stats) / len(stats),
                                "words": sum(s["words_ms"] for s in stats) / len(stats),
                                "host_wall": sum(s["run_ms"] for s in stats) / len(stats),
                                "host_wait": sum(s["sync_ms"] for s in stats) / len(stats),
@@ -562,6 +595,21 @@ def main():
         dist.destroy_process_group()
 
 
+def mark_roofline(stats, lw, W, peak):
+    """The inclusion-marking kernel (only with sw_options.reduce = 1), on the
+    same integer-pipe terms as the meet kernel; None when it did not run."""
+    ms = sum(s["mark_ms"] for s in stats) / len(stats)
+    if ms <= 0:
+        return None
+    steps = sum(s["mark_steps"] for s in stats) / len(stats)
+    rows = sum(s["mark_rows"] for s in stats) / len(stats)
+    ops = steps * 64 * lw + rows * 2 * W * 25
+    achieved = ops / (ms * 1e-3) / 1e12
+    return {"bound": "alu", "kernel": "k_mark_bm", "achieved": achieved, "peak": peak, "unit": "Tops/s",
+            "frac": achieved / peak if peak else None, "ms_per_step": ms, "and_steps_per_step": steps,
+            "rows_transposed_per_step": rows, "pairs_per_step": sum(s["mark_pairs"] for s in stats) / len(stats)}
+
+
 def hbm_peak_gbs():
     try:
         with open(PEAKS_FILE) as fh:
@@ -577,6 +625,69 @@ def hbm_line(ms, nbytes, peak, basis):
     return {"bound": "hbm", "achieved": gbs, "peak": p, "unit": "GB/s", "frac": gbs / p if p else None,
             "peak_basis": f"{src} copy bandwidth", "bytes_per_step": nbytes, "ms_per_step": ms, "traffic": None,
             "bytes_basis": basis}
+
+
+def run_beam(args, d, cfg, sw, torch, local, world):
+    """The beam upper bound of Section 2.1.3 on one large automaton: W
+    warm-up and K timed calls of sw_beam with beam n * ceil(log2 n)."""
+    n = d.shape[1]
+    B = n * int(np.ceil(np.log2(n)))
+    ws = sw.workspace(int(min(args.ws_gb, 64) * (1 << 30)))
+    stream = torch.cuda.Stream()
+
+    def once():
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        R, w = sw.sw_beam(d, B, stream=stream, ws=ws)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return R, w, e0.elapsed_time(e1) * 1e-3
+
+    for _ in range(args.warmup):
+        once()
+    with Clocks(local) as clk:
+        runs = [once() for _ in range(args.steps)]
+    R, w, _ = runs[-1]
+    sec = float(np.mean([x[2] for x in runs]))
+    states = np.arange(n)
+    for a in w:
+        states = d[a][states]
+    return {
+        "metric": "beam upper bounds/sec", "value": 1.0 / sec, "unit": "instances/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": sec * 1e3, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic", "config": cfg,
+        "e2e": {"value": 1.0 / sec, "unit": "instances/s", "h2d_bytes_per_step": int(d.size * 2),
+                "d2h_bytes_per_step": 4 + R},
+        "beam": {"n": n, "beam": B, "R": R, "word_resets": bool(len(np.unique(states)) == 1 and len(w) == R),
+                 "seconds": sec, "mean_r_fit_2.284n^0.515": 2.284 * n ** 0.515},
+        "clocks": clk.summary(), "cpu_baseline": None,
+    }
+
+
+def run_reference_beam(args, d, cfg):
+    """The reference arm of a beam workload: the oracle's beam (oracle.beam)
+    with the same beam size, once, on one host core."""
+    import oracle
+    oracle.build()
+    n = d.shape[1]
+    B = n * int(np.ceil(np.log2(n)))
+    if n > 1000:
+        print(json.dumps({"impl": "reference", "unavailable": "the oracle's beam sorts with a bit-by-bit set "
+                          f"comparison: about 1e10 operations per level at n={n}, hours for one automaton"}),
+              flush=True)
+        return
+    t0 = time.process_time()
+    R, _, _ = oracle.beam(d, B)
+    sec = time.process_time() - t0
+    print(json.dumps({"impl": "reference", "metric": "beam upper bounds/sec", "value": 1.0 / sec,
+                      "unit": "instances/s", "n_gpus": 1, "steps": 1, "warmup": 0, "ms_per_step": sec * 1e3,
+                      "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u64",
+                      "data": "synthetic", "config": cfg, "R": R,
+                      "cpu_baseline": {"value": 1.0 / sec, "unit": "instances/s", "cores": 1, "kind": "oracle",
+                                       "sample": "the one automaton of the workload, oracle.beam, one core"},
+                      "e2e": {"value": 1.0 / sec, "unit": "instances/s", "h2d_bytes_per_step": 0,
+                              "d2h_bytes_per_step": 0}}), flush=True)
 
 
 def run_hard(args, d, cfg, sw, torch, local, world, peak, nsm):
@@ -635,6 +746,7 @@ def run_hard(args, d, cfg, sw, torch, local, world, peak, nsm):
                  "seconds": sec, "fwd_levels": len(fs) - 1, "bwd_levels": len(bs) - 1,
                  "peak_sets": st["arena_peak"], "pairs": st["pairs"], "pairs_per_s": st["pairs"] / sec,
                  "meet_ms": meet_ms, "expand_ms": st["expand_ms"], "compact_ms": st["compact_ms"],
+                 "mark_ms": st["mark_ms"], "mark_pairs": st["mark_pairs"],
                  "balanced_schedule": {"r": r2, "seconds": sec2, "peak_sets": st2["arena_peak"],
                                        "pairs": st2["pairs"], "fwd_levels": len(fs2) - 1,
                                        "bwd_levels": len(bs2) - 1},

@@ -48,6 +48,7 @@ extern "C" {
 
 #define SW_MAX_STATES 576
 #define SW_MAX_LETTERS 255
+#define SW_BEAM_MAX_STATES 8192
 
 enum sw_status {
     SW_OK = 0,
@@ -59,7 +60,8 @@ enum sw_status {
     SW_ECUDA = 6,       /* a CUDA runtime call failed */
     SW_EBUSY = 7,       /* server: no room for the request right now */
     SW_EAGAIN = 8,      /* server: no finished request to report */
-    SW_EINTERNAL = 9    /* a self-check of a result failed */
+    SW_EINTERNAL = 9,   /* a self-check of a result failed */
+    SW_ENOTFOUND = 10   /* sw_beam: no reset word within max_depth levels */
 };
 
 typedef struct sw_automaton *sw_handle;
@@ -150,6 +152,31 @@ int32_t sw_reset_threshold_static(sw_handle h, void *stream, int32_t *r, uint8_t
                                   int32_t word_cap);
 
 /*
+ * Heuristic upper bound R >= r (Section 2.1.3, the cut-off inverse BFS the
+ * paper cites, which it runs with beam size n log n up to n = 5000 in
+ * Section 3).  Level 0 is the n singletons; level d + 1 is made of the
+ * distinct nonempty preimages delta^{-1}(S, a) of the sets of level d
+ * under every letter (candidate c = p*k + a for the set at position p;
+ * among equal sets the smallest c stays), of which only the `beam` largest
+ * are kept (ties: smaller c first), in candidate order.  No history is
+ * kept.  R is the first depth at which Q itself is kept; the word y returned
+ * satisfies delta^{-1}({q}, y) = Q, i.e. delta(Q, y) = {q}, and is checked
+ * on the device.  Takes the automaton directly (n up to SW_BEAM_MAX_STATES,
+ * beyond the exact search's SW_MAX_STATES; delta host int32 [k][n], not
+ * checked for synchronizability).  workspace: caller-owned device memory,
+ * 256-byte aligned; besides a few levels of candidates it holds one int64
+ * per kept set of every level (for the word).  R: host; word: host uint8
+ * [word_cap] or NULL.  Errors: SW_EINVAL, SW_ENOMEM (workspace too small),
+ * SW_ENOTSYNC (a level became empty), SW_ENOTFOUND (no Q within max_depth
+ * levels; a small beam can cycle), SW_EWORDCAP (R > word_cap; R is still
+ * written), SW_ECUDA, SW_EINTERNAL (a table overflowed or the word failed
+ * its check).
+ */
+int32_t sw_beam(int32_t n, int32_t k, const int32_t *delta, void *stream, void *workspace,
+                size_t ws_bytes, int64_t beam, int32_t max_depth, int32_t *R, uint8_t *word,
+                int32_t word_cap);
+
+/*
  * Per-level sizes of the last search that included `h` (single or batched):
  * fwd[i] = size of forward level i for i < *nf, bwd[j] = size of backward
  * level j for j < *nb.  The search computes forward levels 0..i and
@@ -233,6 +260,27 @@ int32_t sw_last_stats(int64_t *pairs, int64_t *candidates, int32_t *iterations,
                       double *sync_ms, double *select_ms, double *update_ms,
                       int32_t *meet_lane_words);
 
+/*
+ * Counters of the calling thread's last search with sw_options.reduce = 1
+ * (the inclusion reductions of Alg. 1, Section 2.1).  mark_ms: device time
+ * of the marking kernel (with timing on); mark_pairs: (set, set) pairs it
+ * covered; mark_steps: its warp-wide AND steps; mark_rows: sets it
+ * transposed into state bitmaps.  Any pointer may be NULL.
+ */
+int32_t sw_last_reduce_stats(double *mark_ms, int64_t *mark_pairs, int64_t *mark_steps,
+                             int64_t *mark_rows);
+
+/*
+ * Calibration of the integer-logic peak the meet and marking kernels are
+ * reported against (no counterpart in the paper).  Runs one CTA of 1024
+ * threads per SM of the current device, each thread issuing independent
+ * chains of three-input LOP3, and writes the LOP3 results retired per SM
+ * clock cycle (timed with the SM's own cycle counter, so independent of
+ * the clock rate).  workspace: device memory of at least 256 + 8 * SMs
+ * bytes, 256-byte aligned.  Errors: SW_EINVAL, SW_ENOMEM, SW_ECUDA.
+ */
+int32_t sw_probe_int_peak(void *stream, void *workspace, size_t ws_bytes, double *lop3_per_clk_per_sm);
+
 /* Enables (1) or disables (0) per-kernel CUDA-event timing for later
  * searches on the calling thread. */
 void sw_set_timing(int32_t on);
@@ -260,6 +308,26 @@ void sw_set_timing(int32_t on);
  *                         at most dir_theta times the backward step's.
  *   set_cost:             cost of producing one set, in pair tests (the
  *                         paper's SetCost, Section 2.1.2).
+ *   reduce:               0 = duplicates and an equality history only (the
+ *                         default; levels as described at the top of this
+ *                         file, and the least reset word); 1 = the inclusion
+ *                         reductions of Alg. 1 (Section 2.1): after the
+ *                         duplicates, every set that is not minimal (BFS) /
+ *                         not maximal (IBFS) among its level, and every
+ *                         superset (BFS) / subset (IBFS) of a set kept at an
+ *                         earlier level of its direction, is removed.  r is
+ *                         the same; the level sizes are those of the reduced
+ *                         lists (a property of the automaton alone, as
+ *                         before); the word is a reset word of length r: the
+ *                         parent chain of the first meeting forward set of
+ *                         the reduced level, then the least suffix, so it
+ *                         depends on the forward depth at which the search
+ *                         met (sw_level_sizes gives it).
+ *   table_cap_slots:      0 (default) or a cap on the slots of every hash
+ *                         table, for testing: an instance whose table can
+ *                         no longer take its sets fails alone with
+ *                         SW_ENOMEM (its result r = -1 in a batch) while
+ *                         the other instances of the call go on.
  * Applies to later searches on the calling thread.
  */
 typedef struct sw_options {
@@ -270,6 +338,8 @@ typedef struct sw_options {
     int32_t meet_lane_words;
     double dir_theta;
     double set_cost;
+    int32_t reduce;
+    int32_t table_cap_slots;
 } sw_options;
 
 void sw_get_options(sw_options *opt);

@@ -26,6 +26,7 @@
 #include <vector>
 
 #include "sw.h"
+#include "sw_internal.h"
 #include "sw_kernels.cuh"
 
 using namespace sw;
@@ -52,10 +53,12 @@ struct Stats {
     int32_t waves = 0, evictions = 0;
     int64_t arena_peak = 0;  // most sets stored at once
     int32_t meet_lw = 0;     // bitmap meet: 64-bit words of the running AND per lane (0: direct test)
+    double mark_ms = 0;      // inclusion reductions: device time of the marking kernel
+    int64_t mark_pairs = 0, mark_steps = 0, mark_rows = 0;  // its pairs, AND steps, rows transposed
 };
 
 thread_local int32_t g_last_error = SW_OK;
-thread_local sw_options g_opt = {0, 0, 0, 4096, 0, 1.0, 8192.0};
+thread_local sw_options g_opt = {0, 0, 0, 4096, 0, 1.0, 8192.0, 0, 0};
 thread_local bool g_timing = false;
 thread_local Stats g_stats;
 // Set only while sw_reset_threshold_static runs: staging buffers then come
@@ -236,8 +239,10 @@ struct Layout {
     int64_t *ntiles;   // meet tiles of the current iteration, then the bitmap kernel's tile counter
     unsigned long long *best;
     uint32_t *word_status;
-    uint32_t *status;
-    unsigned long long *pairs;  // [0] pairs tested, [1] bitmap AND steps, [2] rows transposed
+    uint32_t *status;  // [0] flags of the last launches, [1 + i] flags of instance i
+    int64_t status_n;
+    unsigned long long *pairs;  // meet: [0] pairs tested, [1] bitmap AND steps, [2] rows transposed;
+                                // marking: [3] AND steps, [4] rows transposed, [5] pairs
     uint8_t *word_area;
     int64_t word_area_cap;
     uint16_t *delta16;
@@ -279,7 +284,7 @@ struct Carver {
     }
 };
 
-size_t mirror_bytes_for(int32_t count) { return (size_t)std::max(count, 1) * 1024 + (1 << 20); }
+size_t mirror_bytes_for(int32_t count) { return (size_t)std::max(count, 1) * 4096 + (1 << 20); }
 int64_t word_area_for(int32_t count) { return (int64_t)std::max<size_t>((size_t)std::max(count, 1) * 512, 1 << 20); }
 
 
@@ -292,8 +297,8 @@ size_t small_area_bytes(int32_t count, int64_t delta_elems, int W = 9) {
     add(2 * sizeof(int64_t));
     add(c * sizeof(unsigned long long));
     add(c * sizeof(uint32_t));
-    add(sizeof(uint32_t));
-    add(3 * sizeof(unsigned long long));
+    add((c + 1) * sizeof(uint32_t));
+    add(6 * sizeof(unsigned long long));
     add((size_t)word_area_for(count));
     add((size_t)std::max<int64_t>(delta_elems, 1) * sizeof(uint16_t));
     add((size_t)std::max<int64_t>(delta_elems, 1) * W * sizeof(uint64_t));
@@ -312,8 +317,9 @@ bool carve(void *ws, size_t bytes, int W, int32_t count, int64_t delta_elems, La
     L.ntiles = cv.take<int64_t>(2);
     L.best = cv.take<unsigned long long>(c);
     L.word_status = cv.take<uint32_t>(c);
-    L.status = cv.take<uint32_t>(1);
-    L.pairs = cv.take<unsigned long long>(3);
+    L.status_n = (int64_t)c + 1;
+    L.status = cv.take<uint32_t>(c + 1);
+    L.pairs = cv.take<unsigned long long>(6);
     L.word_area_cap = word_area_for(count);
     L.word_area = cv.take<uint8_t>((size_t)L.word_area_cap);
     L.delta_cap = std::max<int64_t>(delta_elems, 1);
@@ -384,6 +390,9 @@ int sm_count() {
     }
     return g_sm_count;
 }
+
+// rows per tile of the marking kernel
+constexpr int kMarkRows = 4096;
 
 int default_rows(int W) { return W == 1 ? 8 : (W <= 3 ? 4 : 2); }
 int default_btile(int W) { return std::max(64, (4096 / W) & ~1); }
@@ -471,6 +480,25 @@ cudaError_t launch_meet_bm(const MeetJob *jobs, int njobs, int64_t *ntiles, int 
     return cudaGetLastError();
 }
 
+template <int W, int LW, int NT>
+cudaError_t launch_mark_bm(const MarkJob *jobs, int njobs, int64_t *ntiles, int tr_rows, int n_cap, const Layout &L,
+                           cudaStream_t st) {
+    auto kern = k_mark_bm<W, LW, NT>;
+    size_t smem = (size_t)bm_smem_bytes_n(n_cap, LW);
+    static thread_local size_t configured = 0;
+    if (configured < smem) {
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        configured = smem;
+    }
+    int per_sm = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, NT, smem);
+    int64_t grid = (int64_t)sm_count() * std::max(per_sm, 1);
+    kern<<<(unsigned)grid, NT, smem, st>>>(jobs, njobs, ntiles, tr_rows, n_cap, L.sets, L.cand_sets, L.flag, L.meta,
+                                           L.pairs + 3);
+    return cudaGetLastError();
+}
+
 template <int W>
 struct Ops {
     static cudaError_t fill(const FillJob *j, int nj, int64_t maxlen, const Layout &L, cudaStream_t st) {
@@ -512,14 +540,16 @@ struct Ops {
             jobs, nj, ncand, L.delta16, L.pre, L.sets, L.table, L.cand_sets, L.cand_slot, L.status);
         return cudaGetLastError();
     }
-    static cudaError_t compact(const ExpandJob *jobs, int nj, int64_t ncand, const Layout &L, cudaStream_t st) {
+    // phase 0: the plain search; phase 2: after the reductions marked flags
+    static cudaError_t compact(const ExpandJob *jobs, int nj, int64_t ncand, int phase, const Layout &L,
+                               cudaStream_t st) {
         int64_t nblocks = ncand / kScanBlock;
         constexpr int HN = card_slots(W);
         g_stats.launches += 5;
         cudaError_t e = cudaMemsetAsync(L.hist, 0, (size_t)nj * HN * sizeof(uint32_t), st);
         if (e != cudaSuccess) return e;
         k_flag_count<W><<<(unsigned)nblocks, kScanThreads, 0, st>>>(jobs, nj, ncand, L.cand_slot, L.table,
-                                                                    L.cand_sets, L.flag, L.block_cnt, L.hist);
+                                                                    L.cand_sets, L.flag, L.block_cnt, L.hist, phase);
         k_scan_blocks<<<1, 1024, 0, st>>>(nblocks, L.block_cnt, L.block_off);
         k_ge<<<(unsigned)nj, 32, 0, st>>>(jobs, HN, L.hist, L.cursor, L.meta);
         k_compact<W><<<(unsigned)nblocks, kScanThreads, 0, st>>>(jobs, nj, ncand, L.flag, L.block_off, L.cand_sets,
@@ -527,6 +557,19 @@ struct Ops {
                                                                  L.rec, L.cursor);
         k_job_counts<<<(unsigned)((nj + 255) / 256), 256, 0, st>>>(jobs, nj, nblocks, L.block_off, L.counts);
         return cudaGetLastError();
+    }
+    // inclusion reductions: winners (phase 1), then the marking kernel
+    // d_nt: device int64[2] = {mark tiles, 0 (the tile counter)}
+    static cudaError_t mark(const ExpandJob *jobs, int nj, int64_t ncand, const MarkJob *mj, int nmj, int64_t *d_nt,
+                            const MeetCfg &c, const Layout &L, cudaStream_t st) {
+        int64_t nblocks = ncand / kScanBlock;
+        g_stats.launches += 2;
+        k_flag_count<W><<<(unsigned)nblocks, kScanThreads, 0, st>>>(jobs, nj, ncand, L.cand_slot, L.table,
+                                                                    L.cand_sets, L.flag, L.block_cnt, L.hist, 1);
+        if (nmj == 0) return cudaGetLastError();
+        if constexpr (W >= 4 && W <= 7)
+            if (c.lw == 2) return launch_mark_bm<W, 2, 1024>(mj, nmj, d_nt, kMarkRows, c.n_cap, L, st);
+        return launch_mark_bm<W, bm_lanes_words(W), kBmThreads>(mj, nmj, d_nt, kMarkRows, c.n_cap, L, st);
     }
     // tf_rows: forward rows per tile of the bitmap kernel for this launch
     static cudaError_t meet(MeetJob *jobs, int nj, const MeetCfg &c, int tf_rows, const Layout &L, cudaStream_t st) {
@@ -569,19 +612,21 @@ struct Ops {
 };
 
 struct OpTable {
+    cudaError_t (*mark)(const ExpandJob *, int, int64_t, const MarkJob *, int, int64_t *, const MeetCfg &,
+                        const Layout &, cudaStream_t);
     cudaError_t (*pre)(const PreJob *, int, int64_t, const Layout &, cudaStream_t);
     cudaError_t (*fill)(const FillJob *, int, int64_t, const Layout &, cudaStream_t);
     cudaError_t (*roots)(const RootJob *, int, int, const Layout &, cudaStream_t);
     cudaError_t (*rehash)(const RehashSeg *, int, int64_t, const Layout &, cudaStream_t);
     cudaError_t (*expand)(const ExpandJob *, int, int64_t, const Layout &, cudaStream_t);
-    cudaError_t (*compact)(const ExpandJob *, int, int64_t, const Layout &, cudaStream_t);
+    cudaError_t (*compact)(const ExpandJob *, int, int64_t, int, const Layout &, cudaStream_t);
     cudaError_t (*meet)(MeetJob *, int, const MeetCfg &, int, const Layout &, cudaStream_t);
     cudaError_t (*words)(const WordJob *, const int64_t *, int, uint8_t *, const Layout &, cudaStream_t);
 };
 
 template <int W>
 OpTable make_ops() {
-    return {&Ops<W>::pre, &Ops<W>::fill, &Ops<W>::roots, &Ops<W>::rehash, &Ops<W>::expand, &Ops<W>::compact, &Ops<W>::meet,
+    return {&Ops<W>::mark, &Ops<W>::pre, &Ops<W>::fill, &Ops<W>::roots, &Ops<W>::rehash, &Ops<W>::expand, &Ops<W>::compact, &Ops<W>::meet,
             &Ops<W>::words};
 }
 
@@ -631,6 +676,13 @@ float elapsed(cudaEvent_t a, cudaEvent_t b) {
 
 int64_t round_up(int64_t x, int64_t m) { return (x + m - 1) / m * m; }
 
+// Slots of a hash table of `want` slots under sw_options.table_cap_slots
+// (a cap for testing the overflow path; 0 = none).
+int64_t capped_slots(int64_t want) {
+    const int64_t cap = g_opt.table_cap_slots > 0 ? std::max<int64_t>(64, g_opt.table_cap_slots / 64 * 64) : 0;
+    return cap > 0 ? std::min(want, cap) : want;
+}
+
 // cudaStreamSynchronize, with the wait added to the search's statistics.
 cudaError_t wait_stream(cudaStream_t st) {
     auto t0 = std::chrono::steady_clock::now();
@@ -657,10 +709,16 @@ struct Engine {
     uint8_t *out_words = nullptr;
     Staging stg;
     std::vector<int> active, deferred;
+    // Inclusion reductions of Alg. 1 (sw_options.reduce = 1): every
+    // expansion deduplicates in a table of its own (released after the
+    // iteration), and the marking kernel removes non-minimal (BFS) /
+    // non-maximal (IBFS) sets and supersets / subsets of the history.
+    bool reduce = false;
 
     // n_max: no instance the engine will run has more states
     Engine(int W_, int n_max, cudaStream_t s, std::vector<Inst> &insts, const Layout &lay)
         : W(W_), st(s), L(lay), I(insts) {
+        reduce = g_opt.reduce == 1;
         ops = ops_for(W);
         mc = meet_cfg(W, n_max);
         g_stats.meet_lw = mc.algo == 0 ? mc.lw : 0;
@@ -764,7 +822,7 @@ struct Engine {
         size_t cap_jobs = (L.mirror_bytes / 2) / (sizeof(RootJob) + 2 * sizeof(FillJob) + sizeof(PreJob));
         for (size_t t = first; t < ids.size() && ok.size() < cap_jobs; ++t) {
             Inst &x = I[ids[t]];
-            int64_t tc0 = 64, tc1 = round_up(4 * (int64_t)x.n, 64);
+            int64_t tc0 = 64, tc1 = capped_slots(round_up(4 * (int64_t)x.n, 64));
             x.chunks.clear();
             int64_t f = inst_alloc(x, 1);
             int64_t b = f >= 0 ? inst_alloc(x, x.n) : -1;
@@ -807,7 +865,7 @@ struct Engine {
         for (int t = 0; t < nj; ++t) {
             Inst &x = I[ok[t]];
             rj[t] = RootJob{x.lev[0][0].off, x.lev[1][0].off, {x.tab_off[0], x.tab_off[1]},
-                            {x.tab_cap[0], x.tab_cap[1]}, x.n, 0};
+                            {x.tab_cap[0], x.tab_cap[1]}, x.n, ok[t]};
             fj[2 * t] = FillJob{x.tab_off[0], x.tab_cap[0]};
             fj[2 * t + 1] = FillJob{x.tab_off[1], x.tab_cap[1]};
             pj[t] = PreJob{x.delta_off, x.n, x.k};
@@ -847,10 +905,11 @@ struct Engine {
     void plan(std::vector<Sel> &sel) {
         if (planned.size() < I.size()) planned.resize(I.size(), 0);
         int64_t ncand = 0;
-        size_t seg_count = 0;
+        size_t seg_count = 0, mark_count = 0;
         for (const Sel &s : sel) {
             ncand += round_up(s.nc, kScanBlock);
-            if (s.new_tab >= 0) seg_count += I[s.id].lev[s.d].size();
+            if (reduce) mark_count += I[s.id].lev[s.d].size() + 1;
+            else if (s.new_tab >= 0) seg_count += I[s.id].lev[s.d].size();
         }
         // staging bytes of the job arrays, checked before a table grows
         auto staging_fits = [&](size_t bytes) { return bytes + 256 * 8 <= L.mirror_bytes; };
@@ -862,7 +921,17 @@ struct Engine {
             if (ncand + ncp > L.cap_cand) return false;
             size_t segs_here = 0;
             int64_t nt = -1, ntc = 0;
-            if (2 * (x.stored[d] + nc) > x.tab_cap[d]) {  // grow the table: load stays <= 1/2
+            if (reduce) {
+                // a table of this expansion's own (load <= 1/2), and room in
+                // the staging buffer for its marking jobs
+                if (!staging_fits((mark_count + x.lev[d].size() + 1) * sizeof(MarkJob) +
+                                  (sel.size() + 2) * (sizeof(ExpandJob) + sizeof(FillJob) + sizeof(MeetJob))))
+                    return false;
+                ntc = capped_slots(round_up(2 * nc + 64, 64));
+                nt = tab_pool.alloc(ntc);
+                if (nt < 0) return false;
+            } else if (2 * (x.stored[d] + nc) > x.tab_cap[d] && capped_slots(x.tab_cap[d] + 64) > x.tab_cap[d]) {
+                // grow the table: load stays <= 1/2 (unless a cap forbids it)
                 // to a load of 1/6 while small and the pool has room (fewer
                 // rehashes, shorter probes), else to a load of 1/3
                 const int64_t need = x.stored[d] + nc;
@@ -871,11 +940,11 @@ struct Engine {
                                   (sel.size() + 1) * (sizeof(FillJob) + sizeof(MeetJob))))
                     return false;
                 if (need < (int64_t(1) << 22)) {
-                    ntc = round_up(6 * need, 64);
+                    ntc = capped_slots(round_up(6 * need, 64));
                     nt = tab_pool.alloc(ntc);
                 }
                 if (nt < 0) {
-                    ntc = round_up(3 * need, 64);
+                    ntc = capped_slots(round_up(3 * need, 64));
                     nt = tab_pool.alloc(ntc);
                 }
                 if (nt < 0) return false;
@@ -892,7 +961,9 @@ struct Engine {
                 if (nt >= 0) tab_pool.release(nt, ntc);
                 return false;
             }
-            if (nt >= 0) {
+            if (reduce) {
+                mark_count += x.lev[d].size() + 1;
+            } else if (nt >= 0) {
                 tab_pool.release(x.tab_off[d], x.tab_cap[d]);
                 x.tab_off[d] = nt;
                 x.tab_cap[d] = ntc;
@@ -962,19 +1033,22 @@ struct Engine {
             J.parent_cnt = P.cnt;
             J.delta_off = x.delta_off;
             J.dest_off = s.dest;
-            J.tab_off = x.tab_off[s.d];
-            J.tab_cap = x.tab_cap[s.d];
+            J.tab_off = reduce ? s.new_tab : x.tab_off[s.d];
+            J.tab_cap = reduce ? s.new_cap : x.tab_cap[s.d];
             J.ge_off = s.ge;
             J.dir = s.d;
             J.n = x.n;
             J.k = x.k;
-            J.pad = 0;
+            J.inst = s.id;
             cand += round_up(s.nc, kScanBlock);
-            if (s.new_tab >= 0) {
+            if (reduce) {
+                fills.push_back({s.new_tab, s.new_cap});
+                maxfill = std::max(maxfill, s.new_cap);
+            } else if (s.new_tab >= 0) {
                 fills.push_back({s.new_tab, s.new_cap});
                 maxfill = std::max(maxfill, s.new_cap);
                 for (auto &l : x.lev[s.d]) {
-                    segs.push_back({rehash_total, l.off, l.cnt, s.new_tab, s.new_cap, s.d, 0});
+                    segs.push_back({rehash_total, l.off, l.cnt, s.new_tab, s.new_cap, s.d, s.id});
                     rehash_total += l.cnt;
                 }
             }
@@ -984,10 +1058,56 @@ struct Engine {
         RehashSeg *d_segs = nullptr;
         if (!fills.empty()) {
             FillJob *f = stg.take<FillJob>(fills.size(), &d_fill);
-            RehashSeg *g = stg.take<RehashSeg>(segs.size(), &d_segs);
+            RehashSeg *g = stg.take<RehashSeg>(std::max<size_t>(segs.size(), 1), &d_segs);
             if (!stg.ok) return SW_EINTERNAL;
             std::memcpy(f, fills.data(), fills.size() * sizeof(FillJob));
-            std::memcpy(g, segs.data(), segs.size() * sizeof(RehashSeg));
+            if (!segs.empty()) std::memcpy(g, segs.data(), segs.size() * sizeof(RehashSeg));
+        }
+        // inclusion reductions: per job a self-reduction job over its own
+        // candidates and one job per kept level of its direction (the
+        // history); the tiles of all of them are numbered in one range
+        MarkJob *d_mark = nullptr;
+        int64_t *d_mark_nt = nullptr;
+        int n_mark = 0;
+        if (reduce) {
+            size_t cnt = 0;
+            for (const Sel &sl : sel) cnt += I[sl.id].lev[sl.d].size() + 1;
+            MarkJob *mk = stg.take<MarkJob>(std::max<size_t>(cnt, 1), &d_mark);
+            int64_t *nt = stg.take<int64_t>(2, &d_mark_nt);
+            if (!stg.ok) return SW_EINTERNAL;
+            const int64_t kr = (int64_t)2048 * (mc.lw == 4 ? bm_lanes_words(W) : mc.lw);  // chunk rows
+            int64_t tiles = 0;
+            auto add = [&](int64_t r_off, int64_t r_cnt, int r_cand, int64_t c_off, int64_t c_cnt, int c_cand,
+                           int64_t ge, int col, int self) {
+                if (r_cnt <= 0 || c_cnt <= 0) return;
+                MarkJob &M = mk[n_mark++];
+                M.tile_off = tiles;
+                M.ntc = (c_cnt + kr - 1) / kr;
+                M.r_off = r_off;
+                M.r_cnt = r_cnt;
+                M.c_off = c_off;
+                M.c_cnt = c_cnt;
+                M.ge_off = ge;
+                M.r_cand = r_cand;
+                M.c_cand = c_cand;
+                M.col = col;
+                M.self = self;
+                tiles += ((r_cnt + kMarkRows - 1) / kMarkRows) * M.ntc;
+            };
+            for (int t = 0; t < nj; ++t) {
+                const Sel &sl = sel[t];
+                const Inst &x = I[sl.id];
+                const int64_t co = jobs[t].cand_off, cn = sl.nc;
+                if (sl.d == 0) {
+                    add(co, cn, 1, co, cn, 1, -1, 1, 1);
+                    for (const Level &l : x.lev[0]) add(l.off, l.cnt, 0, co, cn, 1, -1, 1, 0);
+                } else {
+                    add(co, cn, 1, co, cn, 1, -1, 0, 1);
+                    for (const Level &l : x.lev[1]) add(co, cn, 1, l.off, l.cnt, 0, l.ge, 0, 0);
+                }
+            }
+            nt[0] = tiles;
+            nt[1] = 0;
         }
         // meet jobs: the size of the level each job produces is filled in on
         // the device (k_meet_prep), so the meet follows without a host sync
@@ -1035,23 +1155,30 @@ struct Engine {
         g_stats.select_ms +=
             std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t_sel).count();
         g_stats.candidates += ncand;
-        if (!fills.empty()) {
-            CK(ops.fill(d_fill, (int)fills.size(), maxfill, L, st));
-            CK(ops.rehash(d_segs, (int)segs.size(), rehash_total, L, st));
-        }
+        if (!fills.empty()) CK(ops.fill(d_fill, (int)fills.size(), maxfill, L, st));
+        if (!segs.empty()) CK(ops.rehash(d_segs, (int)segs.size(), rehash_total, L, st));
+        if (reduce) CK(cudaMemsetAsync(L.pairs + 3, 0, 3 * sizeof(unsigned long long), st));
         if (g_timing) CK(cudaEventRecord(g_ev.ev[0], st));
         CK(ops.expand(d_jobs, nj, ncand, L, st));
         if (g_timing) CK(cudaEventRecord(g_ev.ev[1], st));
-        CK(ops.compact(d_jobs, nj, ncand, L, st));
+        if (reduce) {
+            CK(ops.mark(d_jobs, nj, ncand, d_mark, n_mark, d_mark_nt, mc, L, st));
+            if (g_timing) CK(cudaEventRecord(g_ev.ev[7], st));
+        }
+        CK(ops.compact(d_jobs, nj, ncand, reduce ? 2 : 0, L, st));
         if (g_timing) CK(cudaEventRecord(g_ev.ev[2], st));
         // the new levels' sizes and the status come back before the meet
-        uint64_t *down = (uint64_t *)g_down.get((2 * nj + 5) * sizeof(uint64_t));
+        uint64_t *down = (uint64_t *)g_down.get((2 * nj + 8) * sizeof(uint64_t));
         if (!down) return SW_ECUDA;
         uint64_t *d_status = down + nj, *d_best = down + nj + 1, *d_pairs = down + 2 * nj + 1;
+        uint64_t *d_mark_cnt = down + 2 * nj + 4;
+        if (reduce) d_mark_cnt[0] = d_mark_cnt[1] = d_mark_cnt[2] = 0;
         CK(cudaMemcpyAsync(down, L.counts, nj * sizeof(uint64_t), cudaMemcpyDeviceToHost, st));
         CK(cudaMemcpyAsync(d_status, L.status, sizeof(uint32_t), cudaMemcpyDeviceToHost, st));
         if (counts_event) CK(cudaEventRecord(ev_counts, st));
         CK(cudaMemsetAsync(L.best, 0xFF, nj * sizeof(unsigned long long), st));
+        if (reduce) CK(cudaMemcpyAsync(d_mark_cnt, L.pairs + 3, 3 * sizeof(unsigned long long),
+                                       cudaMemcpyDeviceToHost, st));
         CK(cudaMemsetAsync(L.pairs, 0, 3 * sizeof(unsigned long long), st));
         if (g_timing) CK(cudaEventRecord(g_ev.ev[3], st));
         CK(ops.meet(d_mj, nj, mc, tf_rows, L, st));
@@ -1069,8 +1196,19 @@ struct Engine {
             CK(wait_stream(st));
         }
         if ((uint32_t)(*d_status & 0xFFFFFFFFu) & kStatusTableFull) {
-            (void)wait_stream(st);
-            return SW_EINTERNAL;
+            // a hash table could not take every set of an instance (its
+            // probes ran out): that instance fails with SW_ENOMEM, the others
+            // go on.  Its level of this iteration is incomplete, so neither
+            // the level nor a meet of it is kept.
+            CK(wait_stream(st));
+            uint32_t *inst_flags = (uint32_t *)g_words.get((size_t)L.status_n * sizeof(uint32_t));
+            if (!inst_flags) return SW_ECUDA;
+            CK(cudaMemcpyAsync(inst_flags, L.status, (size_t)L.status_n * sizeof(uint32_t), cudaMemcpyDeviceToHost,
+                               st));
+            CK(wait_stream(st));
+            for (int id : active)
+                if (I[id].state == kActive && (inst_flags[1 + id] & kStatusTableFull)) finish(I[id], kFailed, SW_ENOMEM);
+            CK(cudaMemsetAsync(L.status, 0, (size_t)L.status_n * sizeof(uint32_t), st));
         }
         // new levels; return the unused tail of each destination.  A search
         // with an empty level has run out of new sets: not synchronizing (its
@@ -1079,6 +1217,7 @@ struct Engine {
         for (int t = 0; t < nj; ++t) {
             Sel &s = sel[t];
             Inst &x = I[s.id];
+            if (x.state != kActive) continue;  // failed above: its memory is already released
             int64_t c = (int64_t)down[t];
             inst_shrink(x, s.dest, s.nc, c);
             x.lev[s.d].push_back({s.dest, c, c, s.ge});
@@ -1097,8 +1236,20 @@ struct Engine {
         CK(wait_stream(st));
         if (g_timing) {
             g_stats.expand_ms += elapsed(g_ev.ev[0], g_ev.ev[1]);
-            g_stats.compact_ms += elapsed(g_ev.ev[1], g_ev.ev[2]);
+            if (reduce) {
+                g_stats.mark_ms += elapsed(g_ev.ev[1], g_ev.ev[7]);
+                g_stats.compact_ms += elapsed(g_ev.ev[7], g_ev.ev[2]);
+            } else {
+                g_stats.compact_ms += elapsed(g_ev.ev[1], g_ev.ev[2]);
+            }
             g_stats.meet_ms += elapsed(g_ev.ev[3], g_ev.ev[4]);
+        }
+        if (reduce) {
+            g_stats.mark_steps += (int64_t)d_mark_cnt[0];
+            g_stats.mark_rows += (int64_t)d_mark_cnt[1];
+            g_stats.mark_pairs += (int64_t)d_mark_cnt[2];
+            // this iteration's deduplication tables are done with
+            for (const Sel &sl : sel) tab_pool.release(sl.new_tab, sl.new_cap);
         }
         g_stats.pairs += (int64_t)d_pairs[0];
         g_stats.and_iters += (int64_t)d_pairs[1];
@@ -1119,6 +1270,7 @@ struct Engine {
                                      [&](const Sel &s) {
                                          if (I[s.id].state == kActive) return false;
                                          planned[s.id] = 0;
+                                         if (reduce) tab_pool.release(s.new_tab, s.new_cap);
                                          return true;
                                      }),
                       pending.end());
@@ -1482,6 +1634,13 @@ int32_t static_scratch_ptr(void **out) {
 
 // ==================================================================== C-ABI
 
+int32_t sw_internal_fail(int32_t code) { return fail(code); }
+
+int32_t sw_internal_ok() {
+    g_last_error = SW_OK;
+    return SW_OK;
+}
+
 extern "C" {
 
 int32_t sw_last_error(void) { return g_last_error; }
@@ -1498,6 +1657,7 @@ const char *sw_error_string(int32_t code) {
         case SW_EBUSY: return "no room for the request";
         case SW_EAGAIN: return "no finished request";
         case SW_EINTERNAL: return "internal self-check failed";
+        case SW_ENOTFOUND: return "no reset word found within the depth limit";
         default: return "unknown status";
     }
 }
@@ -1572,7 +1732,7 @@ static int32_t run_instances(std::vector<Inst> &I, const std::vector<uint16_t> *
             maxcnt = std::max(maxcnt, cj[t].count);
         }
         ConvJob *d_cj = (ConvJob *)L.mirror;
-        if (cudaMemsetAsync(L.status, 0, sizeof(uint32_t), st) != cudaSuccess ||
+        if (cudaMemsetAsync(L.status, 0, L.status_n * sizeof(uint32_t), st) != cudaSuccess ||
             cudaMemcpyAsync(d_cj, cj, nI * sizeof(ConvJob), cudaMemcpyHostToDevice, st) != cudaSuccess)
             return SW_ECUDA;
         unsigned gx = (unsigned)std::min<int64_t>((maxcnt + 255) / 256, 64);
@@ -1589,7 +1749,7 @@ static int32_t run_instances(std::vector<Inst> &I, const std::vector<uint16_t> *
             return SW_ECUDA;
         if (*bad) return SW_EINVAL;
     }
-    if (cudaMemsetAsync(L.status, 0, sizeof(uint32_t), st) != cudaSuccess) return SW_ECUDA;
+    if (cudaMemsetAsync(L.status, 0, L.status_n * sizeof(uint32_t), st) != cudaSuccess) return SW_ECUDA;
     int n_max = 1;
     for (auto &x : I) n_max = std::max(n_max, (int)x.n);
     Engine E(W, n_max, st, I, L);
@@ -1728,6 +1888,7 @@ int32_t sw_last_stats(int64_t *pairs, int64_t *candidates, int32_t *iterations, 
                       int32_t *waves, int32_t *evictions, int64_t *arena_peak, int64_t *and_iters,
                       int64_t *rows_transposed, double *words_ms, double *run_ms, double *sync_ms,
                       double *select_ms, double *update_ms, int32_t *meet_lane_words) {
+    if (meet_lane_words) *meet_lane_words = g_stats.meet_lw;
     if (pairs) *pairs = g_stats.pairs;
     if (candidates) *candidates = g_stats.candidates;
     if (iterations) *iterations = g_stats.iterations;
@@ -1764,6 +1925,16 @@ void sw_set_options(const sw_options *opt) {
     if (g_opt.meet_algo != 1) g_opt.meet_algo = 0;
     if (g_opt.meet_f_rows < 0) g_opt.meet_f_rows = 0;
     if (g_opt.meet_lane_words != 4) g_opt.meet_lane_words = 0;
+    if (g_opt.reduce != 1) g_opt.reduce = 0;
+    if (g_opt.table_cap_slots < 0) g_opt.table_cap_slots = 0;
+}
+
+int32_t sw_last_reduce_stats(double *mark_ms, int64_t *mark_pairs, int64_t *mark_steps, int64_t *mark_rows) {
+    if (mark_rows) *mark_rows = g_stats.mark_rows;
+    if (mark_ms) *mark_ms = g_stats.mark_ms;
+    if (mark_pairs) *mark_pairs = g_stats.mark_pairs;
+    if (mark_steps) *mark_steps = g_stats.mark_steps;
+    return SW_OK;
 }
 
 int32_t sw_server_create(void *workspace, size_t ws_bytes, int32_t n_max, int32_t k_max, int32_t max_requests,
@@ -1783,7 +1954,7 @@ int32_t sw_server_create(void *workspace, size_t ws_bytes, int32_t n_max, int32_
     s->opt = g_opt;
     if (!carve(workspace, ws_bytes, s->W, max_requests, (int64_t)max_requests * n_max * k_max, s->L))
         return fail(SW_ENOMEM);
-    if (cudaMemsetAsync(s->L.status, 0, sizeof(uint32_t), s->st) != cudaSuccess ||
+    if (cudaMemsetAsync(s->L.status, 0, s->L.status_n * sizeof(uint32_t), s->st) != cudaSuccess ||
         cudaStreamSynchronize(s->st) != cudaSuccess)
         return fail(SW_ECUDA);
     s->slots.assign((size_t)max_requests, Inst{});

@@ -34,7 +34,8 @@ struct ExpandJob {
     int64_t tab_off;     // the (instance, direction) hash table
     int64_t tab_cap;
     int64_t ge_off;      // backward: where the new level's cardinality table goes
-    int32_t dir, n, k, pad;  // dir 0 forward (images), 1 backward (preimages)
+    int32_t dir, n, k;   // dir 0 forward (images), 1 backward (preimages)
+    int32_t inst;        // the instance (its flags in status[1 + inst])
 };
 
 struct MeetJob {
@@ -106,7 +107,7 @@ __host__ __device__ constexpr int card_slots(int W) { return 64 * W + 2; }
 struct RootJob {
     int64_t f_off, b_off;         // F_0 = {Q} at f_off; B_0 = the n singletons at b_off
     int64_t tab_off[2], tab_cap[2];
-    int32_t n, pad;
+    int32_t n, inst;
 };
 
 struct FillJob {
@@ -117,7 +118,7 @@ struct RehashSeg {
     int64_t flat_off;             // first flat index of this segment
     int64_t set_off, cnt;         // stored sets to re-enter
     int64_t tab_off, tab_cap;     // into this table
-    int32_t dir, pad;
+    int32_t dir, inst;
 };
 
 struct WordJob {
@@ -250,27 +251,36 @@ __device__ __forceinline__ uint64_t next_slot(uint64_t pos, int64_t tab_off, int
     return (pos + 1 == (uint64_t)(tab_off + tab_cap)) ? (uint64_t)tab_off : pos + 1;
 }
 
+// A table that could not take a set: status[0] collects the flags of the
+// whole launch, status[1 + inst] those of the instance, so that the host
+// fails that instance alone.
+__device__ __forceinline__ void table_full(uint32_t *status, int inst) {
+    atomicOr(status, kStatusTableFull);
+    atomicOr(status + 1 + inst, kStatusTableFull);
+}
+
 // Enters the stored set g (no equal set is present) into a table.
 template <int W>
 __device__ __forceinline__ void insert_stored(uint64_t *table, int64_t tab_off, int64_t tab_cap, uint32_t dir,
-                                              const uint64_t (&s)[W], int64_t g, uint32_t *status) {
+                                              const uint64_t (&s)[W], int64_t g, uint32_t *status, int inst) {
     uint64_t pos = (uint64_t)tab_off + __umul64hi(hash_set<W>(dir, s), (uint64_t)tab_cap);
     for (int probe = 0; probe < kMaxProbe; ++probe) {
         unsigned long long old = atomicCAS((unsigned long long *)(table + pos), kEmpty, (unsigned long long)g);
         if (old == kEmpty) return;
         pos = next_slot(pos, tab_off, tab_cap);
     }
-    atomicOr(status, kStatusTableFull);
+    table_full(status, inst);
 }
 
 // The meet kernel's record of a forward set: its first seven states and its
 // cardinality as 16-bit fields (x: s0 | s1 << 16, y: s2 | s3 << 16,
-// z: s4 | s5 << 16, w: s6 | card << 16; missing states are 0xFFFF).
+// z: s4 | s5 << 16, w: s6 | card << 16).  A set of fewer than seven states
+// repeats its first state in the missing fields: ANDing a state's bitmap a
+// second time changes nothing, so the meet kernel walks all seven fields
+// without a bound check.  Forward sets are never empty.
 template <int W>
 __device__ __forceinline__ uint4 row_record(const uint64_t (&s)[W]) {
     uint32_t f[8];
-#pragma unroll
-    for (int i = 0; i < 7; ++i) f[i] = 0xFFFFu;
     int card = 0, got = 0;
 #pragma unroll
     for (int w = 0; w < W; ++w) {
@@ -281,6 +291,9 @@ __device__ __forceinline__ uint4 row_record(const uint64_t (&s)[W]) {
             b &= b - 1;
         }
     }
+#pragma unroll
+    for (int i = 1; i < 7; ++i)
+        if (i >= got) f[i] = f[0];
     f[7] = (uint32_t)card;
     return make_uint4(f[0] | (f[1] << 16), f[2] | (f[3] << 16), f[4] | (f[5] << 16), f[6] | (f[7] << 16));
 }
@@ -319,7 +332,7 @@ __global__ void k_roots(const RootJob *__restrict__ jobs, uint64_t *__restrict__
         }
 #pragma unroll
         for (int w = 0; w < W; ++w) sets[g * W + w] = s[w];
-        insert_stored<W>(table, J.tab_off[dir], J.tab_cap[dir], dir, s, g, status);
+        insert_stored<W>(table, J.tab_off[dir], J.tab_cap[dir], dir, s, g, status, J.inst);
     }
 }
 
@@ -360,7 +373,7 @@ __global__ void k_rehash(const RehashSeg *__restrict__ segs, int nseg, int64_t t
         int64_t g = S.set_off + (t - S.flat_off);
         uint64_t s[W];
         load_set<W>(sets + g * W, s);
-        insert_stored<W>(table, S.tab_off, S.tab_cap, (uint32_t)S.dir, s, g, status);
+        insert_stored<W>(table, S.tab_off, S.tab_cap, (uint32_t)S.dir, s, g, status, S.inst);
     }
 }
 
@@ -435,7 +448,7 @@ __global__ void __launch_bounds__(256) k_expand(
             }
             pos = next_slot(pos, J.tab_off, J.tab_cap);
         }
-        if (probe == kMaxProbe) atomicOr(status, kStatusTableFull);
+        if (probe == kMaxProbe) table_full(status, J.inst);
         cand_slot[c] = result;
     }
 }
@@ -447,15 +460,31 @@ __global__ void __launch_bounds__(256) k_expand(
 // block_cnt[b] = survivors of block b.  The survivors' cardinalities are
 // also counted into hist[job][c] (a block belongs to one job: jobs start on
 // block boundaries).
+//
+// With the inclusion reductions the kernel runs twice.  Phase 1 only sets
+// flag[c] (1 = the candidate won its slot, 0 = not).  The marking kernel
+// then sets flag[c] = 2 on the winners the reductions remove, and phase 2
+// counts and histograms the candidates whose flag is still 1.  Phase 0 is
+// the single pass of the plain search.
 template <int W>
 __global__ void __launch_bounds__(kScanThreads) k_flag_count(
     const ExpandJob *__restrict__ jobs, int njobs, int64_t ncand, const int64_t *__restrict__ cand_slot,
     const uint64_t *__restrict__ table, const uint64_t *__restrict__ cand_sets, uint8_t *__restrict__ flag,
-    uint32_t *__restrict__ block_cnt, uint32_t *__restrict__ hist) {
+    uint32_t *__restrict__ block_cnt, uint32_t *__restrict__ hist, int phase) {
     constexpr int IPT = kScanBlock / kScanThreads;
     constexpr int HN = card_slots(W);
     __shared__ uint32_t sh[HN];
     int64_t base = (int64_t)blockIdx.x * kScanBlock + threadIdx.x * IPT;
+    if (phase == 1) {
+#pragma unroll
+        for (int i = 0; i < IPT; ++i) {
+            int64_t c = base + i;
+            if (c >= ncand) continue;
+            int64_t s = cand_slot[c];
+            flag[c] = (s >= 0 && table[s] == kCand + (uint64_t)c) ? 1 : 0;
+        }
+        return;
+    }
     const int ji = find_job_expand(jobs, njobs, (int64_t)blockIdx.x * kScanBlock);
     for (int i = threadIdx.x; i < HN; i += kScanThreads) sh[i] = 0;
     __syncthreads();
@@ -465,9 +494,13 @@ __global__ void __launch_bounds__(kScanThreads) k_flag_count(
         int64_t c = base + i;
         uint8_t f = 0;
         if (c < ncand) {
-            int64_t s = cand_slot[c];
-            f = (s >= 0 && table[s] == kCand + (uint64_t)c) ? 1 : 0;
-            flag[c] = f;
+            if (phase == 0) {
+                int64_t s = cand_slot[c];
+                f = (s >= 0 && table[s] == kCand + (uint64_t)c) ? 1 : 0;
+                flag[c] = f;
+            } else {
+                f = flag[c] == 1 ? 1 : 0;
+            }
             if (f) {
                 int pc = 0;
 #pragma unroll
@@ -574,7 +607,7 @@ __global__ void __launch_bounds__(kScanThreads) k_compact(
     uint32_t cnt = 0;
 #pragma unroll
     for (int i = 0; i < IPT; ++i) {
-        f[i] = (base + i < ncand) ? flag[base + i] : 0;
+        f[i] = (base + i < ncand && flag[base + i] == 1) ? 1 : 0;  // 2: removed by a reduction
         cnt += f[i];
     }
     // every survivor's place in its cardinality bucket: a block reserves one
@@ -929,7 +962,9 @@ __global__ void __launch_bounds__(NT) k_meet_bm(const MeetJob *__restrict__ jobs
         }
         if (i + NW < i1) fn = __ldg(perm + J.f_off + i + NW);
         int last_card = -1, rows = 0;
-        uint64_t mask[LW];
+        uint32_t mask[2 * LW];
+        // this lane's units of a state bitmap start at sT + q * kStride + lbase
+        const uint32_t *lbase = sT + lane * G::U;
         for (; i < i1; i += NW) {
             // prefetch: the record of the next row, the index of the one after
             uint32_t fnn = 0;
@@ -937,7 +972,9 @@ __global__ void __launch_bounds__(NT) k_meet_bm(const MeetJob *__restrict__ jobs
             if (i + 2 * NW < i1) fnn = __ldg(perm + J.f_off + i + 2 * NW);
             if (i + NW < i1) rn = __ldg(rec + J.f_off + fn);
             // lane 0 reads the shared best; the whole warp follows its decision
-            int pass = (int64_t)(*(volatile unsigned long long *)&s_best >> 32) <= (int64_t)f;
+            // (the walk's votes need every lane of the warp)
+            const int pass = __shfl_sync(
+                0xffffffffu, (int)((int64_t)(*(volatile unsigned long long *)&s_best >> 32) <= (int64_t)f), 0);
             // only the backward sets with at least |X| states can contain X;
             // rows come in increasing cardinality, so the bound changes rarely
             const int card = (int)(r.w >> 16);
@@ -948,87 +985,95 @@ __global__ void __launch_bounds__(NT) k_meet_bm(const MeetJob *__restrict__ jobs
 #pragma unroll
                 for (int j = 0; j < LW; ++j) {
                     int lim = rows - (G::row0(lane, j / HW) + 64 * (j % HW));
-                    mask[j] = lim >= 64 ? ~0ull : (lim > 0 ? ((1ull << lim) - 1) : 0ull);
+                    uint64_t m = lim >= 64 ? ~0ull : (lim > 0 ? ((1ull << lim) - 1) : 0ull);
+                    mask[2 * j] = (uint32_t)m;
+                    mask[2 * j + 1] = (uint32_t)(m >> 32);
                 }
                 last_card = card;
             }
-            if (!__shfl_sync(0xffffffffu, pass, 0)) {
-                uint64_t acc[LW];
+            if (!pass) {
+                // The running intersection, 2*LW 32-bit words per lane.  The
+                // walk ANDs two state bitmaps per step (one three-input LOP3
+                // per word) and votes after the 4th, 6th and 7th listed state
+                // and after every further state.  The record repeats the
+                // first state in the fields of a set with fewer than seven,
+                // so every row walks all seven fields.  From the first vote
+                // on, a lane whose words are all zero skips its loads (its
+                // words stay zero whatever it would have read).
+                uint32_t acc[2 * LW];
 #pragma unroll
-                for (int j = 0; j < LW; ++j) acc[j] = mask[j];
-                bool alive = true;
-                // An AND step with the bitmap of state q: load the lane's
-                // 2*LW words of it (load_frag), AND them into the running
-                // intersection and, from the third step on, vote (apply).
-                // The first three steps skip the vote (a chunk almost never
-                // empties that soon; a row whose states run out before the
-                // third step is settled by the ballot after the walk).
+                for (int j = 0; j < 2 * LW; ++j) acc[j] = mask[j];
                 struct Frag {
                     uint32_t w[2 * LW];
                 };
-                auto load_frag = [&](int q) {
+                auto load_frag = [&](int q, bool on) {
                     Frag fr;
-                    const uint32_t *row = sT + q * G::kStride + lane * G::U;
+                    const uint32_t *row = lbase + q * G::kStride;
 #pragma unroll
                     for (int h = 0; h < G::UPL; ++h) {
                         const uint32_t *p = row + 32 * h * G::U;
                         if constexpr (G::U == 4) {
-                            const uint4 v = *reinterpret_cast<const uint4 *>(p);
+                            uint4 v = make_uint4(0, 0, 0, 0);
+                            if (on) v = *reinterpret_cast<const uint4 *>(p);
                             fr.w[4 * h] = v.x;
                             fr.w[4 * h + 1] = v.y;
                             fr.w[4 * h + 2] = v.z;
                             fr.w[4 * h + 3] = v.w;
                         } else {
-                            const uint2 v = *reinterpret_cast<const uint2 *>(p);
+                            uint2 v = make_uint2(0, 0);
+                            if (on) v = *reinterpret_cast<const uint2 *>(p);
                             fr.w[2 * h] = v.x;
                             fr.w[2 * h + 1] = v.y;
                         }
                     }
                     return fr;
                 };
-                auto apply = [&](const Frag &fr, bool vote) {
-                    uint64_t any = 0;
+                auto and2 = [&](const Frag &x, const Frag &y) {
 #pragma unroll
-                    for (int j = 0; j < LW; ++j) {
-                        acc[j] &= ((uint64_t)fr.w[2 * j + 1] << 32) | fr.w[2 * j];
-                        any |= acc[j];
-                    }
-                    if (vote) alive = __any_sync(0xffffffffu, any != 0);
+                    for (int j = 0; j < 2 * LW; ++j) acc[j] &= x.w[j] & y.w[j];
                 };
-                // state t (< 7) of the record
-                auto listed_state = [&](int t) -> int {
-                    const uint32_t rw = t < 2 ? r.x : t < 4 ? r.y : t < 6 ? r.z : r.w;
-                    return (int)((t & 1) ? (rw >> 16) : (rw & 0xFFFFu));
-                };
-                // The listed states (at most seven), software-pipelined: the
-                // bitmap of step t+1 is loaded before step t's AND and vote.
-                // A row with all seven listed takes a copy of the walk without
-                // the per-step bound check.  `walked` = steps taken.
-                const int listed = min(card, 7);  // >= 1: forward sets are nonempty
-                int walked = listed;
-                auto walk = [&](auto all_listed) {
-                    constexpr bool kAll = decltype(all_listed)::value;
-                    Frag cur = load_frag(listed_state(0));
+                auto and1 = [&](const Frag &x) {
 #pragma unroll
-                    for (int t = 0; t < 7; ++t) {
-                        const bool more = kAll ? (t < 6) : (t + 1 < listed);
-                        Frag nxt;
-                        if (more) nxt = load_frag(listed_state(t + 1 < 7 ? t + 1 : 6));
-                        apply(cur, t >= 2);
-                        if (!more) return;
-                        if (t >= 2 && !alive) {
-                            walked = t + 1;
-                            return;
+                    for (int j = 0; j < 2 * LW; ++j) acc[j] &= x.w[j];
+                };
+                auto lane_alive = [&]() {
+                    uint32_t any = 0;
+#pragma unroll
+                    for (int j = 0; j < 2 * LW; ++j) any |= acc[j];
+                    return any != 0;
+                };
+                const int s0 = (int)(r.x & 0xFFFFu), s1 = (int)(r.x >> 16);
+                const int s2 = (int)(r.y & 0xFFFFu), s3 = (int)(r.y >> 16);
+                const int s4 = (int)(r.z & 0xFFFFu), s5 = (int)(r.z >> 16);
+                const int s6 = (int)(r.w & 0xFFFFu);
+                uint32_t steps = 4;
+                bool la, alive;
+                {
+                    const Frag a0 = load_frag(s0, true), b0 = load_frag(s1, true);
+                    const Frag a1 = load_frag(s2, true), b1 = load_frag(s3, true);
+                    and2(a0, b0);
+                    and2(a1, b1);
+                }
+                la = lane_alive();
+                {
+                    const Frag a2 = load_frag(s4, la), b2 = load_frag(s5, la);
+                    alive = __any_sync(0xffffffffu, la);
+                    if (alive) {
+                        steps = 6;
+                        and2(a2, b2);
+                        la = lane_alive();
+                        const Frag a3 = load_frag(s6, la);
+                        alive = __any_sync(0xffffffffu, la);
+                        if (alive) {
+                            steps = 7;
+                            and1(a3);
+                            la = lane_alive();
+                            alive = __any_sync(0xffffffffu, la);
                         }
-                        cur = nxt;
                     }
-                };
-                if (listed == 7) walk(std::true_type{});
-                else walk(std::false_type{});
-                uint32_t steps = (uint32_t)walked;
+                }
                 if (alive && card > 7) {
                     // the states after the seventh, from the set itself
-                    const int s6 = (int)(r.w & 0xFFFFu);
                     uint64_t x[W];
                     load_set<W>(sets + (J.f_off + f) * W, x);
 #pragma unroll
@@ -1040,7 +1085,9 @@ __global__ void __launch_bounds__(NT) k_meet_bm(const MeetJob *__restrict__ jobs
                         while (bits && alive) {
                             const int q = lo + __ffs(bits) - 1;
                             bits &= bits - 1;
-                            apply(load_frag(q), true);
+                            and1(load_frag(q, la));
+                            la = lane_alive();
+                            alive = __any_sync(0xffffffffu, la);
                             ++steps;
                         }
                     }
@@ -1048,25 +1095,23 @@ __global__ void __launch_bounds__(NT) k_meet_bm(const MeetJob *__restrict__ jobs
                 my_iters += steps;
                 my_pairs += (unsigned long long)rows;
                 if (alive) {  // every state of X processed: X lies inside the surviving sets
-                    uint64_t any = 0;
-#pragma unroll
-                    for (int j = 0; j < LW; ++j) any |= acc[j];
-                    unsigned ball = __ballot_sync(0xffffffffu, any != 0);
+                    unsigned ball = __ballot_sync(0xffffffffu, la);
                     if (lane == __ffs(ball) - 1) {
                         // first nonzero word of the lane, by selects (no
                         // dynamic index, which would put acc in local memory)
                         int j = 0;
-                        uint64_t v = acc[0];
+                        uint32_t v = acc[0];
 #pragma unroll
-                        for (int t = 1; t < LW; ++t)
+                        for (int t = 1; t < 2 * LW; ++t)
                             if (v == 0) {
                                 v = acc[t];
                                 j = t;
                             }
+                        const int j64 = j >> 1;
                         unsigned long long key =
                             ((unsigned long long)f << 32) |
-                            (unsigned long long)(b0 + G::row0(lane, j / HW) + 64 * (j % HW) +
-                                                 __ffsll((long long)v) - 1);
+                            (unsigned long long)(b0 + G::row0(lane, j64 / HW) + 64 * (j64 % HW) + 32 * (j & 1) +
+                                                 __ffs(v) - 1);
                         atomicMin(&s_best, key);
                         atomicMin(best + J.slot, key);
                     }
@@ -1084,6 +1129,267 @@ __global__ void __launch_bounds__(NT) k_meet_bm(const MeetJob *__restrict__ jobs
         if (my_iters) atomicAdd(and_iters, my_iters);
     }
     if (threadIdx.x == 0 && my_rows) atomicAdd(rows_transposed, my_rows);
+}
+
+// ------------------------------------------------------------ inclusion reductions
+
+// One unit of work of the reductions of Alg. 1 (Section 2.1).  rows x chunk
+// are tested for inclusion "row inside chunk set":
+//   col = 0: the rows are the targets: a row that lies inside some set of
+//            the chunk is removed (IBFS: self-reduction to maximal sets,
+//            and subsets of the history);
+//   col = 1: the chunk sets are the targets: a chunk set that contains some
+//            row is removed (BFS: self-reduction to minimal sets, and
+//            supersets of the history).
+// A side lies either in candidate space (the winners of this expansion,
+// flag 1 = kept so far, 2 = removed, 0 = not a winner) or in the arena (a
+// kept level of an earlier depth).  self = 1 when both sides are the same
+// candidates: a set is not its own witness, and since the winners are
+// distinct sets, inclusion between two of them is proper.  Witnesses are
+// never filtered by marks (a removed set still removes its supersets or
+// subsets, as in Alg. 1 where both reductions test the deduplicated list),
+// so the result does not depend on the order in which tiles run; targets
+// already removed are skipped.
+struct MarkJob {
+    int64_t tile_off;          // first tile of this job
+    int64_t ntc;               // chunk tiles
+    int64_t r_off, r_cnt;      // rows: candidate ids (r_cand) or arena indices
+    int64_t c_off, c_cnt;      // chunk: candidate ids (c_cand) or arena indices
+    int64_t ge_off;            // arena chunk sorted by decreasing cardinality: its ge table, or -1
+    int32_t r_cand, c_cand, col, self;
+};
+
+// Inclusion marking by vertical bitmaps, as k_meet_bm: the chunk (up to
+// Bm<LW>::kRows sets) is transposed into one bitmap per state in shared
+// memory, and a warp ANDs the bitmaps of a row's states, two per step (a
+// three-input LOP3 per word), voting after the fourth state and after every
+// second one from there on.  A row whose intersection survives lies inside
+// the surviving chunk sets.  Tiles of tr_rows rows x one chunk are drawn
+// from the counter ntiles_p[1] (zeroed by the host).  counters: [0] AND
+// steps, [1] chunk rows transposed, [2] (row, chunk set) pairs covered.
+template <int W, int LW, int NT>
+__global__ void __launch_bounds__(NT) k_mark_bm(const MarkJob *__restrict__ jobs, int njobs,
+                                                int64_t *__restrict__ ntiles_p, int tr_rows, int n_cap,
+                                                const uint64_t *__restrict__ sets,
+                                                const uint64_t *__restrict__ cand_sets, uint8_t *flag,
+                                                const int32_t *__restrict__ meta,
+                                                unsigned long long *counters) {
+    constexpr int HN = card_slots(W);
+    using G = Bm<LW>;
+    constexpr int HW = G::U / 2;
+    constexpr int NW = NT / 32;
+    constexpr int NWORD = 2 * LW;  // 32-bit words of the running AND per lane
+    const int64_t ntiles = ntiles_p[0];
+    unsigned long long *next_tile = reinterpret_cast<unsigned long long *>(ntiles_p + 1);
+    extern __shared__ __align__(16) uint32_t sT[];
+    __shared__ int64_t s_tile;
+    __shared__ int s_job, s_maxcard;
+    __shared__ uint32_t s_hit[32 * NWORD];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    unsigned long long my_steps = 0, my_rows = 0, my_pairs = 0;
+    for (;;) {
+        if (threadIdx.x == 0) s_tile = (int64_t)atomicAdd(next_tile, 1ull);
+        __syncthreads();
+        const int64_t tile = s_tile;
+        if (tile >= ntiles) break;
+        if (threadIdx.x == 0) {
+            int lo = 0, hi = njobs - 1;
+            while (lo < hi) {
+                int mid = (lo + hi + 1) >> 1;
+                if (jobs[mid].tile_off <= tile) lo = mid; else hi = mid - 1;
+            }
+            s_job = lo;
+            s_maxcard = -1;
+        }
+        for (int t = threadIdx.x; t < 32 * NWORD; t += NT) s_hit[t] = 0;
+        __syncthreads();
+        const MarkJob &J = jobs[s_job];
+        const int64_t local = tile - J.tile_off;
+        const int64_t tr = local / J.ntc;
+        const int64_t b0 = (local - tr * J.ntc) * G::kRows;
+        const int nb = (int)min((int64_t)G::kRows, J.c_cnt - b0);
+        const int64_t i0 = tr * tr_rows, i1 = min(i0 + tr_rows, J.r_cnt);
+        // 1. the chunk, transposed; in candidate space only the winners
+        //    (witnesses) or the winners still kept (targets) take part
+        const uint64_t *csrc = J.c_cand ? cand_sets : sets;
+        int wmax = -1;
+        for (int g = warp; g < G::kRows / 32; g += NW) {
+            const int row = g * 32 + lane;
+            uint64_t y[W];
+#pragma unroll
+            for (int w = 0; w < W; ++w) y[w] = 0;
+            if (row < nb) {
+                const int64_t idx = J.c_off + b0 + row;
+                bool in = true;
+                if (J.c_cand) {
+                    const uint8_t fl = flag[idx];
+                    in = J.col ? fl == 1 : fl != 0;
+                }
+                if (in) {
+                    load_set<W>(csrc + idx * W, y);
+                    int pc = 0;
+#pragma unroll
+                    for (int w = 0; w < W; ++w) pc += __popcll(y[w]);
+                    wmax = max(wmax, pc);
+                }
+            }
+#pragma unroll
+            for (int h = 0; h < 2 * W; ++h) {
+                if (32 * h >= n_cap) break;
+                uint32_t v = (h & 1) ? (uint32_t)(y[h >> 1] >> 32) : (uint32_t)y[h >> 1];
+                uint32_t c = warp_transpose32(v, lane);
+                if (32 * h + lane < n_cap) sT[G::pos(32 * h + lane, g)] = c;
+            }
+        }
+        for (int o = 16; o; o >>= 1) wmax = max(wmax, __shfl_xor_sync(0xffffffffu, wmax, o));
+        if (lane == 0 && wmax >= 0) atomicMax(&s_maxcard, wmax);
+        if (threadIdx.x == 0) my_rows += (unsigned long long)max(nb, 0);
+        __syncthreads();
+        const int maxcard = s_maxcard;
+        const int32_t *ge = J.ge_off >= 0 ? meta + J.ge_off : nullptr;
+        const uint64_t *rsrc = J.r_cand ? cand_sets : sets;
+        const uint32_t *lbase = sT + lane * G::U;
+        uint32_t hit[NWORD];
+#pragma unroll
+        for (int j = 0; j < NWORD; ++j) hit[j] = 0;
+        // 2. rows, one per warp at a time
+        for (int64_t i = i0 + warp; maxcard >= 0 && i < i1; i += NW) {
+            const int64_t ridx = J.r_off + i;
+            if (J.r_cand) {
+                // lane 0 reads the flag; the warp follows its decision
+                int fl = lane == 0 ? (int)flag[ridx] : 0;
+                fl = __shfl_sync(0xffffffffu, fl, 0);
+                if (J.col ? fl == 0 : fl != 1) continue;
+            }
+            uint64_t x[W];
+            load_set<W>(rsrc + ridx * W, x);
+            int card = 0;
+#pragma unroll
+            for (int w = 0; w < W; ++w) card += __popcll(x[w]);
+            if (card > maxcard) continue;  // no chunk set is large enough to hold it
+            int limit = nb;
+            if (ge) limit = (int)min((int64_t)nb, (int64_t)__ldg(ge + min(card, HN - 1)) - b0);
+            if (limit <= 0) continue;
+            uint32_t acc[NWORD];
+#pragma unroll
+            for (int j = 0; j < LW; ++j) {
+                const int lim = limit - (G::row0(lane, j / HW) + 64 * (j % HW));
+                const uint64_t m = lim >= 64 ? ~0ull : (lim > 0 ? ((1ull << lim) - 1) : 0ull);
+                acc[2 * j] = (uint32_t)m;
+                acc[2 * j + 1] = (uint32_t)(m >> 32);
+            }
+            if (J.self) {  // a set is not its own witness
+                const int64_t own = ridx - (J.c_off + b0);
+                if (own >= 0 && own < nb) {
+                    const int o = (int)own;
+                    const int u = o / (32 * G::U), e = o % (32 * G::U);
+                    if ((u & 31) == lane) {
+                        const int jj = 2 * ((u >> 5) * HW + e / 64) + ((e % 64) >> 5);
+#pragma unroll
+                        for (int t = 0; t < NWORD; ++t)
+                            if (t == jj) acc[t] &= ~(1u << (e & 31));
+                    }
+                }
+            }
+            my_pairs += (unsigned long long)limit;
+            struct Frag {
+                uint32_t w[NWORD];
+            };
+            auto load_frag = [&](int q, bool on) {
+                Frag fr;
+                const uint32_t *rowp = lbase + q * G::kStride;
+#pragma unroll
+                for (int h = 0; h < G::UPL; ++h) {
+                    const uint32_t *p = rowp + 32 * h * G::U;
+                    if constexpr (G::U == 4) {
+                        uint4 v = make_uint4(0, 0, 0, 0);
+                        if (on) v = *reinterpret_cast<const uint4 *>(p);
+                        fr.w[4 * h] = v.x;
+                        fr.w[4 * h + 1] = v.y;
+                        fr.w[4 * h + 2] = v.z;
+                        fr.w[4 * h + 3] = v.w;
+                    } else {
+                        uint2 v = make_uint2(0, 0);
+                        if (on) v = *reinterpret_cast<const uint2 *>(p);
+                        fr.w[2 * h] = v.x;
+                        fr.w[2 * h + 1] = v.y;
+                    }
+                }
+                return fr;
+            };
+            bool la = true, alive = true;
+            int walked = 0, pend = -1;
+            // the row's states in increasing order, ANDed two at a time
+#pragma unroll
+            for (int h = 0; h < 2 * W; ++h) {
+                uint32_t bits = (h & 1) ? (uint32_t)(x[h >> 1] >> 32) : (uint32_t)x[h >> 1];
+                while (bits && alive) {
+                    const int q = 32 * h + __ffs(bits) - 1;
+                    bits &= bits - 1;
+                    if (pend < 0) {
+                        pend = q;
+                        continue;
+                    }
+                    const Frag a = load_frag(pend, la), b = load_frag(q, la);
+#pragma unroll
+                    for (int j = 0; j < NWORD; ++j) acc[j] &= a.w[j] & b.w[j];
+                    pend = -1;
+                    walked += 2;
+                    if (walked >= 4) {
+                        uint32_t any = 0;
+#pragma unroll
+                        for (int j = 0; j < NWORD; ++j) any |= acc[j];
+                        la = any != 0;
+                        alive = __any_sync(0xffffffffu, la);
+                    }
+                }
+            }
+            if (alive && pend >= 0) {
+                const Frag a = load_frag(pend, la);
+#pragma unroll
+                for (int j = 0; j < NWORD; ++j) acc[j] &= a.w[j];
+                ++walked;
+            }
+            if (alive) {
+                uint32_t any = 0;
+#pragma unroll
+                for (int j = 0; j < NWORD; ++j) any |= acc[j];
+                la = any != 0;
+                alive = __any_sync(0xffffffffu, la);
+            }
+            my_steps += (unsigned long long)walked;
+            if (alive) {  // every state of the row processed: it lies inside the surviving chunk sets
+                if (!J.col) {
+                    if (lane == 0) flag[ridx] = 2;
+                } else {
+#pragma unroll
+                    for (int j = 0; j < NWORD; ++j) hit[j] |= acc[j];
+                }
+            }
+        }
+        if (J.col) {
+#pragma unroll
+            for (int j = 0; j < NWORD; ++j)
+                if (hit[j]) atomicOr(&s_hit[lane * NWORD + j], hit[j]);
+            __syncthreads();
+            for (int t = threadIdx.x; t < 32 * NWORD; t += NT) {
+                uint32_t bits = s_hit[t];
+                const int ln = t / NWORD, jj = t % NWORD, j = jj >> 1;
+                const int base = G::row0(ln, j / HW) + 64 * (j % HW) + 32 * (jj & 1);
+                while (bits) {
+                    const int b = base + __ffs(bits) - 1;
+                    bits &= bits - 1;
+                    if (b < nb) flag[J.c_off + b0 + b] = 2;
+                }
+            }
+        }
+        __syncthreads();
+    }
+    if (lane == 0) {
+        if (my_steps) atomicAdd(counters, my_steps);
+        if (my_pairs) atomicAdd(counters + 2, my_pairs);
+    }
+    if (threadIdx.x == 0 && my_rows) atomicAdd(counters + 1, my_rows);
 }
 
 // ------------------------------------------------------------ word recovery

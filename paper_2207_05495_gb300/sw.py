@@ -18,8 +18,9 @@ _LIB_PATH = os.path.join(_HERE, "libsw.so")
 _lib = None
 
 SW_OK, SW_EINVAL, SW_ENOTSYNC, SW_ENOMEM, SW_ETIMEOUT, SW_EWORDCAP, SW_ECUDA, SW_EBUSY, SW_EAGAIN, \
-    SW_EINTERNAL = range(10)
+    SW_EINTERNAL, SW_ENOTFOUND = range(11)
 SW_MAX_STATES = 576
+SW_BEAM_MAX_STATES = 8192
 SW_MAX_LETTERS = 255
 
 
@@ -34,7 +35,8 @@ class sw_options(ctypes.Structure):
     _fields_ = [("meet_algo", ctypes.c_int32), ("meet_rows_per_thread", ctypes.c_int32),
                 ("meet_b_tile", ctypes.c_int32), ("meet_f_rows", ctypes.c_int32),
                 ("meet_lane_words", ctypes.c_int32),
-                ("dir_theta", ctypes.c_double), ("set_cost", ctypes.c_double)]
+                ("dir_theta", ctypes.c_double), ("set_cost", ctypes.c_double), ("reduce", ctypes.c_int32),
+                ("table_cap_slots", ctypes.c_int32)]
 
 
 def lib():
@@ -65,6 +67,12 @@ def lib():
         L.sw_batch_device.restype = i32
         L.sw_last_stats.argtypes = [p] * 19
         L.sw_last_stats.restype = i32
+        L.sw_beam.argtypes = [i32, i32, p, p, p, sz, i64, i32, p, p, i32]
+        L.sw_beam.restype = i32
+        L.sw_probe_int_peak.argtypes = [p, p, sz, p]
+        L.sw_probe_int_peak.restype = i32
+        L.sw_last_reduce_stats.argtypes = [p, p, p, p]
+        L.sw_last_reduce_stats.restype = i32
         L.sw_set_timing.argtypes = [i32]
         L.sw_set_timing.restype = None
         L.sw_get_options.argtypes = [p]
@@ -169,6 +177,23 @@ def sw_reset_threshold_static(h: Automaton, stream=None, word_cap: int = 1 << 16
     return int(r[0]), word[: r[0]].tolist()
 
 
+def sw_beam(delta, beam: int, stream=None, ws=None, max_depth: int = 1 << 16):
+    """(R, word) of the cut-off inverse BFS keeping the `beam` largest
+    preimages of every depth (an upper bound R >= r).  delta: [k][n] int32
+    array, n up to SW_BEAM_MAX_STATES."""
+    d = np.ascontiguousarray(np.asarray(delta, dtype=np.int32))
+    k, n = d.shape
+    if ws is None:
+        ws = workspace(1 << 30)
+    R = np.zeros(1, np.int32)
+    word = np.zeros(max(max_depth, 1), np.uint8)
+    p, nb = _ws_args(ws)
+    rc = lib().sw_beam(n, k, _ptr(d), _stream(stream), p, nb, beam, max_depth, _ptr(R), _ptr(word), len(word))
+    if rc != SW_OK:
+        raise SwError(rc, "sw_beam")
+    return int(R[0]), word[: R[0]].tolist()
+
+
 def sw_level_sizes(h: Automaton, cap: int = 1 << 16):
     """(forward sizes, backward sizes) of the last search of h."""
     f = np.zeros(cap, np.int64)
@@ -218,6 +243,14 @@ def sw_batch_device(n, k, d_delta, delta_off, stream=None, ws=None, d_r=None, d_
 
 
 def sw_last_stats() -> dict:
+    """Counters of the calling thread's last search (sw_last_stats), with
+    the marking kernel's (sw_last_reduce_stats) under the keys mark_*."""
+    d = _last_stats()
+    d.update(sw_last_reduce_stats())
+    return d
+
+
+def _last_stats() -> dict:
     pairs, cand, launches, peak = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int64()
     iters, rows = ctypes.c_int64(), ctypes.c_int64()
     wms, rms, sms = ctypes.c_double(), ctypes.c_double(), ctypes.c_double()
@@ -236,6 +269,23 @@ def sw_last_stats() -> dict:
             "and_iters": iters.value, "rows_transposed": rows.value, "words_ms": wms.value,
             "run_ms": rms.value, "sync_ms": sms.value, "select_ms": sel.value, "update_ms": upd.value,
             "meet_lane_words": lw.value}
+
+
+def sw_last_reduce_stats() -> dict:
+    ms, pairs, steps, rows = ctypes.c_double(), ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int64()
+    lib().sw_last_reduce_stats(ctypes.byref(ms), ctypes.byref(pairs), ctypes.byref(steps), ctypes.byref(rows))
+    return {"mark_ms": ms.value, "mark_pairs": pairs.value, "mark_steps": steps.value, "mark_rows": rows.value}
+
+
+def sw_probe_int_peak(stream=None) -> float:
+    """LOP3 results retired per SM clock (sw_probe_int_peak)."""
+    ws = workspace(1 << 20)
+    v = ctypes.c_double()
+    p, nb = _ws_args(ws)
+    rc = lib().sw_probe_int_peak(_stream(stream), p, nb, ctypes.byref(v))
+    if rc != SW_OK:
+        raise SwError(rc, "sw_probe_int_peak")
+    return v.value
 
 
 def sw_set_timing(on: bool) -> None:

@@ -92,4 +92,6 @@ def test_cpu_baseline_line_counts_every_instance():
     cpu = bench.cpu_baseline_line(ds, 4, 2)
     assert cpu["cores"] == 2 and cpu["kind"] == "oracle"
     assert cpu["value"] > 0 and cpu["single_thread"] > 0
-    assert "seeds 0, 2, ... 6" in cpu["sample"]
+    assert "indices 0, 2, ... 6" in cpu["sample"] and "whole workload" in cpu["sample"]
+    cpu = bench.cpu_baseline_line(ds, 4, 2, n_max=15)  # n = 12 .. 15: four instances
+    assert "indices 0, 1, ... 3" in cpu["sample"] and "stratum n <= 15 (4 of 8" in cpu["sample"]

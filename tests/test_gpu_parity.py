@@ -327,3 +327,32 @@ def test_server_results_equal_alone(sw):
         assert code == 0 and (r, w) == alone[i] == want[i], i
     assert stats["admitted_while_2"] >= 1, stats
     assert stats["max_active"] >= 3, stats
+
+
+def test_table_overflow_fails_only_its_instance(sw, ws):
+    """A host-side cap on every hash table (sw_options.table_cap_slots, a
+    test knob; no device fault) makes the tables of the two large automata
+    overflow: those two fail alone with SW_ENOMEM (r = -1), every other
+    instance of the same batch is oracle-exact, and without the cap the
+    same batch succeeds."""
+    small = [gen.random_automaton(int(n), 2, 40 + i) for i, n in enumerate([5, 8, 11, 13, 9, 16, 12, 7, 15, 10])]
+    big = [gen.random_automaton(110, 2, 3), gen.random_automaton(120, 2, 4)]
+    ds = small[:5] + [big[0]] + small[5:] + [big[1]]
+    hs = [sw.load(d) for d in ds]
+    old = sw.sw_get_options()
+    o = sw.sw_get_options()
+    o.table_cap_slots = 2048
+    sw.sw_set_options(o)
+    try:
+        r, w = sw.sw_batch(hs, ws=ws, raise_on_error=False)
+        assert sw.lib().sw_last_error() == sw.SW_ENOMEM
+    finally:
+        sw.sw_set_options(old)
+    for i, d in enumerate(ds):
+        if d.shape[1] >= 110:
+            assert r[i] == -1 and w[i] is None, i
+        else:
+            assert (int(r[i]), w[i]) == oracle.bidir(d)[:2], i
+    r2, w2 = sw.sw_batch(hs, ws=ws)
+    for i in (5, len(ds) - 1):
+        assert (int(r2[i]), w2[i]) == oracle.bidir(ds[i])[:2]
