@@ -314,21 +314,26 @@ static int check_automaton(int n, int k, const int32_t *delta) {
     return 0;
 }
 
-static void level_root_Q(level_t *L, int n, int W) {
-    uint64_t s[16];
+static int level_root_Q(level_t *L, int n, int W) {
+    uint64_t *s = (uint64_t *)malloc((size_t)W * sizeof(uint64_t));
+    if (!s) return OR_ENOMEM;
     set_clear(s, W);
     for (int q = 0; q < n; q++) set_add(s, q);
-    level_push(L, s, -1, 0, W);
+    int rc = level_push(L, s, -1, 0, W);
+    free(s);
+    return rc;
 }
 
 static int level_root_singletons(level_t *L, int n, int W) {
-    uint64_t s[16];
+    uint64_t *s = (uint64_t *)malloc((size_t)W * sizeof(uint64_t));
+    if (!s) return OR_ENOMEM;
     int rc = level_reserve(L, n, W);
     for (int q = 0; !rc && q < n; q++) {
         set_clear(s, W);
         set_add(s, q);
         rc = level_push(L, s, -1, 0, W);
     }
+    free(s);
     return rc;
 }
 
@@ -400,8 +405,8 @@ int oracle_forward(int n, int k, const int32_t *delta, int64_t max_sets, int32_t
     level_t *lv = (level_t *)calloc((size_t)cap, sizeof(level_t));
     history_t H = {0, NULL};
     if (!lv) return OR_ENOMEM;
-    level_root_Q(&lv[0], n, W);
-    rc = history_init(&H, &lv[0], n, W);
+    rc = level_root_Q(&lv[0], n, W);
+    if (!rc) rc = history_init(&H, &lv[0], n, W);
     int64_t stored = 1;
     int64_t hit = (n == 1) ? 0 : -1;
     while (!rc && hit < 0) {
@@ -449,7 +454,7 @@ int oracle_level_sizes(int n, int k, const int32_t *delta, int dir, int32_t dept
     int W = words_for(n);
     level_t cur = {0}, next = {0};
     history_t H = {0, NULL};
-    if (dir == 0) level_root_Q(&cur, n, W);
+    if (dir == 0) rc = level_root_Q(&cur, n, W);
     else rc = level_root_singletons(&cur, n, W);
     if (!rc) rc = history_init(&H, &cur, n, W);
     int64_t stored = cur.count;
@@ -527,8 +532,8 @@ int oracle_bidir(int n, int k, const int32_t *delta, int64_t max_sets, int32_t *
     history_t HF = {0, NULL}, HB = {0, NULL};
     if (!F || !B) { free(F); free(B); return OR_ENOMEM; }
     int i = 0, j = 0;
-    level_root_Q(&F[0], n, W);
-    rc = level_root_singletons(&B[0], n, W);
+    rc = level_root_Q(&F[0], n, W);
+    if (!rc) rc = level_root_singletons(&B[0], n, W);
     if (!rc) rc = history_init(&HF, &F[0], n, W);
     if (!rc) rc = history_init(&HB, &B[0], n, W);
     int64_t stored = F[0].count + B[0].count;
@@ -675,7 +680,7 @@ int oracle_reduced_level_sizes(int n, int k, const int32_t *delta, int dir, int3
     int W = words_for(n);
     level_t *lv = (level_t *)calloc((size_t)depth + 1, sizeof(level_t));
     if (!lv) return OR_ENOMEM;
-    if (dir == 0) level_root_Q(&lv[0], n, W);
+    if (dir == 0) rc = level_root_Q(&lv[0], n, W);
     else rc = level_root_singletons(&lv[0], n, W);
     int64_t stored = lv[0].count;
     if (!rc) sizes[0] = lv[0].count;
@@ -713,8 +718,8 @@ int oracle_bidir_reduced(int n, int k, const int32_t *delta, int64_t max_sets, i
     level_t *B = (level_t *)calloc((size_t)cap, sizeof(level_t));
     if (!F || !B) { free(F); free(B); return OR_ENOMEM; }
     int i = 0, j = 0;
-    level_root_Q(&F[0], n, W);
-    rc = level_root_singletons(&B[0], n, W);
+    rc = level_root_Q(&F[0], n, W);
+    if (!rc) rc = level_root_singletons(&B[0], n, W);
     int64_t stored = F[0].count + B[0].count;
     int64_t hit = rc ? -1 : first_meet(&F[0], &B[0], n, W);
     while (!rc && hit < 0) {
