@@ -56,7 +56,7 @@ def _load():
         lib.oracle_bidir.argtypes = [ctypes.c_int, ctypes.c_int, p, i64, p, p, i32, p, p, p, p, i32]
         lib.oracle_is_synchronizing.argtypes = [ctypes.c_int, ctypes.c_int, p]
         lib.oracle_reduced_level_sizes.argtypes = [ctypes.c_int, ctypes.c_int, p, ctypes.c_int, i32, i64, p]
-        lib.oracle_bidir_reduced.argtypes = [ctypes.c_int, ctypes.c_int, p, i64, i32, p, p, i32, p, p, p, p, i32]
+        lib.oracle_bidir_reduced.argtypes = [ctypes.c_int, ctypes.c_int, p, i64, i32, i32, p, p, i32, p, p, p, p, i32]
         lib.oracle_beam.argtypes = [ctypes.c_int, ctypes.c_int, p, i64, i32, p, p, i32, p, i32, p]
         lib.oracle_beam.restype = ctypes.c_int
         for f in (lib.oracle_brute, lib.oracle_forward, lib.oracle_level_sizes, lib.oracle_bidir,
@@ -144,10 +144,13 @@ def reduced_level_sizes(delta, direction: int, depth: int, max_sets: int = 50_00
     return sizes.tolist()
 
 
-def bidir_reduced(delta, fwd_depth: int = -1, max_sets: int = 50_000_000, word_cap: int = 1 << 20):
+def bidir_reduced(delta, fwd_depth: int = -1, dirs: int = 3, max_sets: int = 50_000_000,
+                  word_cap: int = 1 << 20):
     """O3: (r, word, fwd_sizes, bwd_sizes) by Alg. 1 with the inclusion
     reductions.  fwd_depth >= 0 fixes the forward depth of the meet (the
-    word depends on it; r and the sizes do not)."""
+    word depends on it; r and the sizes do not).  dirs: 1 reduces the BFS
+    side only, 2 the IBFS side only, 3 both; an unreduced side keeps the
+    equality history."""
     d, n, k = _delta(delta)
     r = np.zeros(1, np.int32)
     w = np.zeros(word_cap, np.uint8)
@@ -156,8 +159,8 @@ def bidir_reduced(delta, fwd_depth: int = -1, max_sets: int = 50_000_000, word_c
     bs = np.zeros(cap, np.int64)
     nf = np.zeros(1, np.int32)
     nb = np.zeros(1, np.int32)
-    rc = _load().oracle_bidir_reduced(n, k, _ptr(d), max_sets, fwd_depth, _ptr(r), _ptr(w), word_cap, _ptr(fs),
-                                      _ptr(nf), _ptr(bs), _ptr(nb), cap)
+    rc = _load().oracle_bidir_reduced(n, k, _ptr(d), max_sets, fwd_depth, dirs, _ptr(r), _ptr(w), word_cap,
+                                      _ptr(fs), _ptr(nf), _ptr(bs), _ptr(nb), cap)
     if rc:
         raise OracleError(rc, "oracle_bidir_reduced")
     return int(r[0]), w[: r[0]].tolist(), fs[: nf[0]].tolist(), bs[: nb[0]].tolist()

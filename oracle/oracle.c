@@ -703,10 +703,13 @@ int oracle_reduced_level_sizes(int n, int k, const int32_t *delta, int dir, int3
  * split.  fwd_depth < 0: the side with fewer sets steps (equal sizes step
  * forward); fwd_depth >= 0: forward steps until the forward depth is
  * fwd_depth, then backward steps (so the first meet is at i = fwd_depth
- * when fwd_depth <= r).  The word is the parent chain of the first meeting
- * forward set in list order followed by the least suffix (least_suffix).
+ * when fwd_depth <= r).  dirs: bit 0 reduces the BFS side, bit 1 the IBFS
+ * side; a side that is not reduced keeps duplicate deletion and the
+ * equality history (as oracle_bidir).  The word is the parent chain of the
+ * first meeting forward set in list order followed by the least suffix
+ * (least_suffix).
  */
-int oracle_bidir_reduced(int n, int k, const int32_t *delta, int64_t max_sets, int32_t fwd_depth,
+int oracle_bidir_reduced(int n, int k, const int32_t *delta, int64_t max_sets, int32_t fwd_depth, int32_t dirs,
                          int32_t *r_out, uint8_t *word, int32_t word_cap, int64_t *fsizes, int32_t *nf,
                          int64_t *bsizes, int32_t *nb, int32_t sizes_cap) {
     int rc = check_automaton(n, k, delta);
@@ -718,21 +721,26 @@ int oracle_bidir_reduced(int n, int k, const int32_t *delta, int64_t max_sets, i
     level_t *B = (level_t *)calloc((size_t)cap, sizeof(level_t));
     if (!F || !B) { free(F); free(B); return OR_ENOMEM; }
     int i = 0, j = 0;
+    history_t HF = {0, NULL}, HB = {0, NULL}; /* equality histories of a side that is not reduced */
     rc = level_root_Q(&F[0], n, W);
     if (!rc) rc = level_root_singletons(&B[0], n, W);
+    if (!rc && !(dirs & 1)) rc = history_init(&HF, &F[0], n, W);
+    if (!rc && !(dirs & 2)) rc = history_init(&HB, &B[0], n, W);
     int64_t stored = F[0].count + B[0].count;
     int64_t hit = rc ? -1 : first_meet(&F[0], &B[0], n, W);
     while (!rc && hit < 0) {
         if (i + 1 >= cap || j + 1 >= cap) { rc = OR_ETOOBIG; break; }
         int dir = fwd_depth >= 0 ? (i < fwd_depth ? 0 : 1) : (F[i].count <= B[j].count ? 0 : 1);
         if (dir == 0) {
-            rc = expand_reduced(n, k, delta, 0, &F[i], F, i + 1, &F[i + 1], max_sets - stored);
+            if (dirs & 1) rc = expand_reduced(n, k, delta, 0, &F[i], F, i + 1, &F[i + 1], max_sets - stored);
+            else rc = expand(n, k, delta, 0, &F[i], &HF, &F[i + 1], max_sets - stored);
             if (rc) break;
             i++;
             stored += F[i].count;
             if (F[i].count == 0) { rc = OR_ENOTSYNC; break; }
         } else {
-            rc = expand_reduced(n, k, delta, 1, &B[j], B, j + 1, &B[j + 1], max_sets - stored);
+            if (dirs & 2) rc = expand_reduced(n, k, delta, 1, &B[j], B, j + 1, &B[j + 1], max_sets - stored);
+            else rc = expand(n, k, delta, 1, &B[j], &HB, &B[j + 1], max_sets - stored);
             if (rc) break;
             j++;
             stored += B[j].count;
@@ -758,7 +766,7 @@ int oracle_bidir_reduced(int n, int k, const int32_t *delta, int64_t max_sets, i
         }
     }
     for (int d = 0; d < cap; d++) { level_free(&F[d]); level_free(&B[d]); }
-    free(F); free(B);
+    free(F); free(B); free(HF.sets); free(HB.sets);
     return rc;
 }
 

@@ -288,17 +288,34 @@ def test_reduced_level_sizes_all_binary_n3():
             assert oracle.reduced_level_sizes(d, direction, 4) == want
 
 
-def reduced_word_by_definition(delta, r, i):
+def plain_levels_by_definition(delta, direction, depth):
+    """Level i without reductions: the sets reachable at depth i and at no
+    smaller depth (duplicates and the equality history removed)."""
+    R = reachable_by_depth(delta, direction, depth)
+    out, earlier = [], set()
+    for i in range(depth + 1):
+        out.append(R[i] - earlier)
+        earlier |= R[i]
+    return out
+
+
+def side_levels(delta, direction, depth, reduced):
+    return (reduced_levels_by_definition if reduced else plain_levels_by_definition)(delta, direction, depth)
+
+
+def reduced_word_by_definition(delta, r, i, dirs=3):
     """The reduced search's word for the split (i, r - i), by enumeration:
     x = the lexicographically least word of length i all of whose prefixes
     (x itself included) reach a kept set of their depth and whose set lies
     inside some kept backward set of depth r - i; then the least y of
-    length r - i with |delta(delta(Q, x), y)| = 1."""
+    length r - i with |delta(delta(Q, x), y)| = 1.  dirs: which sides are
+    reduced (bit 0 BFS, bit 1 IBFS); a plain side keeps the sets first
+    reached at each depth."""
     dl = [list(map(int, row)) for row in np.asarray(delta)]
     k, n = len(dl), len(dl[0])
     j = r - i
-    F = reduced_levels_by_definition(delta, 0, i)
-    B = reduced_levels_by_definition(delta, 1, j)[j]
+    F = side_levels(delta, 0, i, dirs & 1)
+    B = side_levels(delta, 1, j, dirs & 2)[j]
     for x in itertools.product(range(k), repeat=i):
         s = frozenset(range(n))
         ok = s in F[0]
@@ -330,6 +347,22 @@ def test_reduced_search_r_word_and_sizes(d):
         assert wi == reduced_word_by_definition(d, r, i)
     # a split with no forward step gives the least reset word of all
     assert oracle.bidir_reduced(d, fwd_depth=0)[1] == wb
+
+
+@pytest.mark.parametrize("dirs", [1, 2])
+@pytest.mark.parametrize("d", _small_random(10, (3, 7), (2, 3), 77))
+def test_one_side_reduced_search(d, dirs):
+    # only one side reduced: that side's levels follow the reduced
+    # characterisation, the other side's the plain one; r and the word of
+    # every split as the enumeration says
+    rb, wb = oracle.brute(d, 16)
+    r, w, fs, bs = oracle.bidir_reduced(d, dirs=dirs)
+    assert r == rb and resets(d, w)
+    assert fs == [len(L) for L in side_levels(d, 0, len(fs) - 1, dirs & 1)]
+    assert bs == [len(L) for L in side_levels(d, 1, len(bs) - 1, dirs & 2)]
+    for i in range(r + 1):
+        ri, wi, fi, bi = oracle.bidir_reduced(d, fwd_depth=i, dirs=dirs)
+        assert ri == r and wi == reduced_word_by_definition(d, r, i, dirs)
 
 
 @pytest.mark.parametrize("n", [2, 3, 5, 8, 12])
