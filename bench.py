@@ -10,10 +10,10 @@ least shortest reset word of every instance.
   e2e           the same through sw_batch with host buffers (automata copied
                 in and results copied out inside the timed region).
   roofline      the meet kernel (the dominant kernel), integer-ALU bound:
-                int32 operations it performs (64 per 64-bit lane word of a
-                warp-wide AND step, 25 per 32-bit word of each transposed
-                backward row) against 128 int32 lanes/SM x SMs x maximum SM
-                clock.
+                the 32-bit ANDs of its walk (one per bitmap word per state)
+                plus 25 operations per 32-bit word of each transposed
+                backward row, against 2 ANDs per three-input LOP3 x the
+                measured LOP3 rate per SM clock x SMs x maximum SM clock.
   roofline_hbm  the expansion and compaction kernels against the measured
                 HBM copy bandwidth: algorithmic bytes per candidate and per
                 stored set over their event time.
@@ -52,10 +52,8 @@ sys.path.insert(0, ROOT)
 from paper_2207_05495_gb300 import gen  # noqa: E402
 
 PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
-# 32-bit integer logic (LOP3) results per clock per SM on sm_103: 4 SM
-# sub-partitions x 32 lanes (a LOP3 issue probe measured 113/clk/SM with its
-# loop overhead included).  Shared memory: 32 banks x 4 B per clock per SM.
-INT32_LANES_PER_SM = 128
+# Shared memory: 32 banks x 4 B per clock per SM.  (The integer peak is
+# measured at run time by sw_probe_int_peak: LOP3 per SM clock.)
 SMEM_BYTES_PER_CLK_SM = 128
 SM_MAX_MHZ_FALLBACK = 2070.0
 N_SMS_NOMINAL = 152
@@ -64,8 +62,9 @@ N_SMS_NOMINAL = 152
 # dram__bytes_write.sum) of single meet launches of the first 512 automata
 # of this workload; the full workload is too large for a multi-pass
 # capture, so its traffic per launch is this figure times the rows one
-# launch transposes.  None until captured for the current kernel.
-MEET_DRAM_BYTES_PER_ROW = None
+# launch transposes (profiles/meet_traffic_batch512_c3.md; recaptured
+# whenever the kernel changes).
+MEET_DRAM_BYTES_PER_ROW = 13.4
 
 
 def rank_seeds(rank: int, count: int) -> range:
@@ -341,7 +340,7 @@ def main():
                     choices=["c3", "c1", "cerny", "hard300", "hard400", "hard500", "hard570", "beam1000", "beam2000",
                              "beam5000"])
     ap.add_argument("--ws-gb", type=float, default=160.0)
-    ap.add_argument("--cpu-sample", type=int, default=32,
+    ap.add_argument("--cpu-sample", type=int, default=160,
                     help="instances of the fixed sample the CPU oracle runs to completion")
     ap.add_argument("--cpu-full", action="store_true",
                     help="CPU sample spread over the whole workload instead of the stratum n <= --ref-n-max "
@@ -355,6 +354,8 @@ def main():
     ap.add_argument("--opt", action="append", default=[],
                     help="override a search option after tuning, e.g. --opt meet_lane_words=4")
     ap.add_argument("--serve-requests", type=int, default=1500)
+    ap.add_argument("--one-schedule", action="store_true",
+                    help="hard workloads: skip the second (balanced) schedule")
     args = ap.parse_args()
 
     rank = int(os.environ.get("RANK", "0"))
@@ -416,8 +417,11 @@ def main():
         cfg["options"] = "library defaults"
     props = torch.cuda.get_device_properties(local)
     nsm = props.multi_processor_count
-    lop3_probe = sw.sw_probe_int_peak()  # LOP3 per SM clock, measured
-    peak = INT32_LANES_PER_SM * nsm * SM_MAX_MHZ_FALLBACK * 1e6 / 1e12
+    # the integer peak of the meet and marking kernels: the measured LOP3
+    # issue rate per SM clock, times the two bitmap-word ANDs one
+    # three-input LOP3 retires, times SMs and the maximum SM clock
+    lop3_probe = sw.sw_probe_int_peak()
+    peak = 2 * lop3_probe * nsm * SM_MAX_MHZ_FALLBACK * 1e6 / 1e12
     smem_peak = SMEM_BYTES_PER_CLK_SM * nsm * SM_MAX_MHZ_FALLBACK * 1e6 / 1e12
     hbm_peak = hbm_peak_gbs()
     if args.workload.startswith("beam"):
@@ -565,9 +569,8 @@ def main():
                      "smem_tbs": smem_bytes / sec / 1e12 if sec > 0 else 0.0, "smem_peak_tbs": smem_peak,
                      "pairs_per_step": pairs, "pairs_per_sec_in_kernel": pairs / sec if sec > 0 else 0.0,
                      "launches_per_step": launches, "avg_launch_ms": meet_ms / max(launches, 1),
-                     "peak_basis": f"{INT32_LANES_PER_SM} int32 lanes/SM x {nsm} SMs x "
-                                   f"{SM_MAX_MHZ_FALLBACK:.0f} MHz (max SM clock); a LOP3 probe measured "
-                                   f"{lop3_probe:.1f} per SM clock (sw_probe_int_peak)",
+                     "peak_basis": f"2 ANDs per three-input LOP3 x {lop3_probe:.1f} LOP3/SM/clock measured "
+                                   f"(sw_probe_int_peak) x {nsm} SMs x {SM_MAX_MHZ_FALLBACK:.0f} MHz (max SM clock)",
                      "lop3_probe_per_clk_per_sm": lop3_probe},
         "roofline_hbm": hbm,
         "roofline_mark": mark_roofline(stats, lw, W, peak),
@@ -690,6 +693,42 @@ def run_reference_beam(args, d, cfg):
                               "d2h_bytes_per_step": 0}}), flush=True)
 
 
+def tensor_core_pairs_per_s(torch, K: int, M: int = 16384, N: int = 16384):
+    """The ceiling of a tensor-core meet, measured: X subset of Y as a dense
+    0/1 contraction (|X intersect Y| = |X|), here a library fp8 GEMM
+    (torch._scaled_mm, e4m3 x e4m3 with fp32 accumulation, exact for
+    counts <= 576) of M forward rows by N backward sets over K = 64W state
+    columns, without the epilogue a meet would add.  Returns pairs/s and
+    TFLOP/s, best of 20 after warm-up; None where fp8 GEMMs are missing."""
+    try:
+        a = (torch.rand(M, K, device="cuda") < 0.3).to(torch.float8_e4m3fn)
+        b = (torch.rand(N, K, device="cuda") < 0.5).to(torch.float8_e4m3fn)
+        one = torch.ones((), device="cuda")
+
+        def f():
+            return torch._scaled_mm(a, b.t(), scale_a=one, scale_b=one, out_dtype=torch.float32)
+
+        c = f()
+        want = a[:64].float() @ b[:64].float().t()
+        exact = bool(torch.equal(c[:64, :64], want))
+        for _ in range(3):
+            f()
+        best = None
+        for _ in range(20):
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record()
+            f()
+            e1.record()
+            torch.cuda.synchronize()
+            t = e0.elapsed_time(e1) * 1e-3
+            best = t if best is None else min(best, t)
+        return {"gemm": "torch._scaled_mm e4m3 x e4m3 -> fp32", "shape_mkn": [M, K, N], "exact": exact,
+                "seconds": best, "pairs_per_s": M * N / best, "tflops": 2.0 * M * N * K / best / 1e12}
+    except (RuntimeError, TypeError, AttributeError) as e:
+        return {"gemm": "torch._scaled_mm e4m3", "unavailable": str(e)[:200]}
+
+
 def run_hard(args, d, cfg, sw, torch, local, world, peak, nsm):
     """A hard single instance: W warm-up and K timed searches with the
     library's direction rule, then one with "expand the smaller side"
@@ -719,12 +758,15 @@ def run_hard(args, d, cfg, sw, torch, local, world, peak, nsm):
             runs.append(once())
     r, w, _, st, (fs, bs) = runs[-1]
     sec = float(np.mean([x[2] for x in runs]))
-    old = sw.sw_get_options()
-    o = sw.sw_get_options()
-    o.set_cost = 1e9
-    sw.sw_set_options(o)
-    r2, w2, sec2, st2, (fs2, bs2) = once()
-    sw.sw_set_options(old)
+    if args.one_schedule:
+        r2, w2, sec2, st2, (fs2, bs2) = r, w, sec, st, (fs, bs)
+    else:
+        old = sw.sw_get_options()
+        o = sw.sw_get_options()
+        o.set_cost = 1e9
+        sw.sw_set_options(o)
+        r2, w2, sec2, st2, (fs2, bs2) = once()
+        sw.sw_set_options(old)
     sw.sw_set_timing(False)
     states = np.arange(n)
     for a in w:
@@ -745,12 +787,14 @@ def run_hard(args, d, cfg, sw, torch, local, world, peak, nsm):
         "hard": {"n": n, "r": r, "word_resets": bool(len(np.unique(states)) == 1 and len(w) == r),
                  "seconds": sec, "fwd_levels": len(fs) - 1, "bwd_levels": len(bs) - 1,
                  "peak_sets": st["arena_peak"], "pairs": st["pairs"], "pairs_per_s": st["pairs"] / sec,
+                 "pairs_per_s_in_meet_kernel": pairs / (meet_ms * 1e-3) if meet_ms > 0 else None,
                  "meet_ms": meet_ms, "expand_ms": st["expand_ms"], "compact_ms": st["compact_ms"],
                  "mark_ms": st["mark_ms"], "mark_pairs": st["mark_pairs"],
                  "balanced_schedule": {"r": r2, "seconds": sec2, "peak_sets": st2["arena_peak"],
                                        "pairs": st2["pairs"], "fwd_levels": len(fs2) - 1,
                                        "bwd_levels": len(bs2) - 1},
-                 "schedules_agree": bool(agree)},
+                 "schedules_agree": None if args.one_schedule else bool(agree),
+                 "tensor_core_meet_ceiling": tensor_core_pairs_per_s(torch, 64 * W)},
         "roofline": {"bound": "alu", "kernel": "k_meet_bm", "achieved": achieved, "peak": peak, "unit": "Tops/s",
                      "frac": achieved / peak if peak else None, "traffic": None, "lane_words": lw},
         "clocks": clk.summary(), "gpu_launches": int(st["launches"]), "cpu_baseline": None,

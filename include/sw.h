@@ -311,18 +311,21 @@ void sw_set_timing(int32_t on);
  *   reduce:               0 = duplicates and an equality history only (the
  *                         default; levels as described at the top of this
  *                         file, and the least reset word); 1 = the inclusion
- *                         reductions of Alg. 1 (Section 2.1): after the
- *                         duplicates, every set that is not minimal (BFS) /
- *                         not maximal (IBFS) among its level, and every
- *                         superset (BFS) / subset (IBFS) of a set kept at an
- *                         earlier level of its direction, is removed.  r is
- *                         the same; the level sizes are those of the reduced
- *                         lists (a property of the automaton alone, as
- *                         before); the word is a reset word of length r: the
- *                         parent chain of the first meeting forward set of
- *                         the reduced level, then the least suffix, so it
- *                         depends on the forward depth at which the search
- *                         met (sw_level_sizes gives it).
+ *                         reductions of Alg. 1 (Section 2.1) on both sides:
+ *                         after the duplicates, every set that is not
+ *                         minimal (BFS) / not maximal (IBFS) among its
+ *                         level, and every superset (BFS) / subset (IBFS) of
+ *                         a set kept at an earlier level of its direction,
+ *                         is removed; 2 = the same on the BFS side only; 3 =
+ *                         on the IBFS side only (the other side keeps the
+ *                         equality history).  r is the same; a reduced
+ *                         side's level sizes are those of its reduced lists
+ *                         (a property of the automaton alone, as before);
+ *                         with the BFS side reduced the word is a reset word
+ *                         of length r: the parent chain of the first meeting
+ *                         forward set of the reduced level, then the least
+ *                         suffix, so it depends on the forward depth at
+ *                         which the search met (sw_level_sizes gives it).
  *   table_cap_slots:      0 (default) or a cap on the slots of every hash
  *                         table, for testing: an instance whose table can
  *                         no longer take its sets fails alone with

@@ -271,7 +271,7 @@ __global__ void __launch_bounds__(kBThreads) k_beam_compact(int64_t ncand, int n
                                                             const uint64_t *__restrict__ cand,
                                                             const int32_t *__restrict__ card,
                                                             uint64_t *__restrict__ next, int64_t *__restrict__ link,
-                                                            unsigned long long *hit) {
+                                                            int64_t cap, unsigned long long *hit) {
     __shared__ uint32_t ws[kBThreads / 32];
     const int64_t c0 = (int64_t)blockIdx.x * kBBlock + 2 * threadIdx.x;
     uint32_t f[2];
@@ -282,6 +282,7 @@ __global__ void __launch_bounds__(kBThreads) k_beam_compact(int64_t ncand, int n
         if (!f[i]) continue;
         const int64_t c = c0 + i;
         const int64_t pos = (int64_t)keep_off[blockIdx.x] + r[i];
+        if (pos >= cap) continue;  // more kept sets than the level buffers hold: the host fails the call
         for (int w = 0; w < nw; ++w) next[pos * nw + w] = cand[c * nw + w];
         link[pos] = c;
         if (card[c] == n) atomicMin(hit, (unsigned long long)pos);
@@ -352,7 +353,11 @@ extern "C" int32_t sw_beam(int32_t n, int32_t k, const int32_t *delta, void *str
     }
     cudaStream_t st = (cudaStream_t)stream;
     const int nw = (n + 63) / 64;
-    const int64_t lev_cap = std::max<int64_t>(beam, n);
+    // the level buffers hold min(beam, what about 60% of the workspace
+    // allows) sets; a level that keeps more fails the call with SW_ENOMEM
+    const double per_set = 16.0 * nw + k * (8.0 * nw + 13.0 + 16.0);
+    const int64_t fit = (int64_t)(0.6 * (double)ws_bytes / per_set);
+    const int64_t lev_cap = std::max<int64_t>(n, std::min<int64_t>(beam, fit));
     const int64_t ncap = lev_cap * k;
     const int64_t nblk = (ncap + kBBlock - 1) / kBBlock;
     int64_t tab_cap = 2 * ncap + 64;
@@ -418,7 +423,7 @@ extern "C" int32_t sw_beam(int32_t n, int32_t k, const int32_t *delta, void *str
     for (int d = 1; d <= max_depth; ++d) {
         const int64_t nc = m * k;
         const int64_t nb = (nc + kBBlock - 1) / kBBlock;
-        if (links_used + std::min(nc, beam) > L.links_cap) return sw_internal_fail(SW_ENOMEM);
+        if (links_used + std::min(nc, lev_cap) > L.links_cap) return sw_internal_fail(SW_ENOMEM);
         level_link[d] = links_used;
         BCK(cudaMemsetAsync(L.table, 0xFF, (size_t)tab_cap * 8, st));
         BCK(cudaMemsetAsync(L.hist, 0, (size_t)(n + 1) * 4, st));
@@ -434,13 +439,14 @@ extern "C" int32_t sw_beam(int32_t n, int32_t k, const int32_t *delta, void *str
         k_beam_rank<<<(unsigned)nb, kBThreads, 0, st>>>(nc, 1, L.card, L.flag, L.cut, eq_off, L.bcnt);
         k_beam_scan<<<1, 1024, 0, st>>>(nb, L.bcnt, keep_off);
         k_beam_compact<<<(unsigned)nb, kBThreads, 0, st>>>(nc, n, nw, L.flag, keep_off, L.cand, L.card, L.lev[1 - cur],
-                                                           L.links + links_used, L.hit);
+                                                           L.links + links_used, lev_cap, L.hit);
         BCK(cudaGetLastError());
         BCK(cudaMemcpyAsync(&down.kept, keep_off + nb, 8, cudaMemcpyDeviceToHost, st));
         BCK(cudaMemcpyAsync(&down.hit, L.hit, 8, cudaMemcpyDeviceToHost, st));
         BCK(cudaMemcpyAsync(&down.status, L.status, 4, cudaMemcpyDeviceToHost, st));
         BCK(cudaStreamSynchronize(st));
         if (down.status) return sw_internal_fail(SW_EINTERNAL);  // a level's table overflowed
+        if ((int64_t)down.kept > lev_cap) return sw_internal_fail(SW_ENOMEM);
         m = (int64_t)down.kept;
         links_used += m;
         cur = 1 - cur;

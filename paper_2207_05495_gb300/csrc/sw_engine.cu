@@ -586,6 +586,11 @@ struct Ops {
                 if (c.lw == 2)
                     return launch_meet_bm<W, 2, 1024>(jobs, nj, ntiles, tf_rows, c.n_cap, L.sets, L.perm, L.rec,
                                                       L.best, L.pairs, L.pairs + 1, L.pairs + 2, L.meta, st);
+            // 2048-set chunks of more than 438 states take more than half of
+            // an SM's shared memory: one CTA per SM, so give it 1024 threads
+            if constexpr (W >= 4)
+                return launch_meet_bm<W, 1, 1024>(jobs, nj, ntiles, tf_rows, c.n_cap, L.sets, L.perm, L.rec,
+                                                  L.best, L.pairs, L.pairs + 1, L.pairs + 2, L.meta, st);
             return launch_meet_bm<W, bm_lanes_words(W), kBmThreads>(jobs, nj, ntiles, tf_rows, c.n_cap, L.sets,
                                                                     L.perm, L.rec, L.best, L.pairs, L.pairs + 1,
                                                                     L.pairs + 2, L.meta, st);
@@ -709,16 +714,21 @@ struct Engine {
     uint8_t *out_words = nullptr;
     Staging stg;
     std::vector<int> active, deferred;
-    // Inclusion reductions of Alg. 1 (sw_options.reduce = 1): every
-    // expansion deduplicates in a table of its own (released after the
-    // iteration), and the marking kernel removes non-minimal (BFS) /
-    // non-maximal (IBFS) sets and supersets / subsets of the history.
+    // Inclusion reductions of Alg. 1 (sw_options.reduce 1: both sides, 2:
+    // the BFS side, 3: the IBFS side): an expansion of a reduced side
+    // deduplicates in a table of its own (released after the iteration),
+    // and the marking kernel removes non-minimal (BFS) / non-maximal (IBFS)
+    // sets and supersets / subsets of that side's history.  rdir[d]: side d
+    // is reduced.
     bool reduce = false;
+    bool rdir[2] = {false, false};
 
     // n_max: no instance the engine will run has more states
     Engine(int W_, int n_max, cudaStream_t s, std::vector<Inst> &insts, const Layout &lay)
         : W(W_), st(s), L(lay), I(insts) {
-        reduce = g_opt.reduce == 1;
+        rdir[0] = g_opt.reduce == 1 || g_opt.reduce == 2;
+        rdir[1] = g_opt.reduce == 1 || g_opt.reduce == 3;
+        reduce = rdir[0] || rdir[1];
         ops = ops_for(W);
         mc = meet_cfg(W, n_max);
         g_stats.meet_lw = mc.algo == 0 ? mc.lw : 0;
@@ -908,7 +918,7 @@ struct Engine {
         size_t seg_count = 0, mark_count = 0;
         for (const Sel &s : sel) {
             ncand += round_up(s.nc, kScanBlock);
-            if (reduce) mark_count += I[s.id].lev[s.d].size() + 1;
+            if (rdir[s.d]) mark_count += I[s.id].lev[s.d].size() + 1;
             else if (s.new_tab >= 0) seg_count += I[s.id].lev[s.d].size();
         }
         // staging bytes of the job arrays, checked before a table grows
@@ -921,7 +931,7 @@ struct Engine {
             if (ncand + ncp > L.cap_cand) return false;
             size_t segs_here = 0;
             int64_t nt = -1, ntc = 0;
-            if (reduce) {
+            if (rdir[d]) {
                 // a table of this expansion's own (load <= 1/2), and room in
                 // the staging buffer for its marking jobs
                 if (!staging_fits((mark_count + x.lev[d].size() + 1) * sizeof(MarkJob) +
@@ -961,7 +971,7 @@ struct Engine {
                 if (nt >= 0) tab_pool.release(nt, ntc);
                 return false;
             }
-            if (reduce) {
+            if (rdir[d]) {
                 mark_count += x.lev[d].size() + 1;
             } else if (nt >= 0) {
                 tab_pool.release(x.tab_off[d], x.tab_cap[d]);
@@ -1033,15 +1043,15 @@ struct Engine {
             J.parent_cnt = P.cnt;
             J.delta_off = x.delta_off;
             J.dest_off = s.dest;
-            J.tab_off = reduce ? s.new_tab : x.tab_off[s.d];
-            J.tab_cap = reduce ? s.new_cap : x.tab_cap[s.d];
+            J.tab_off = rdir[s.d] ? s.new_tab : x.tab_off[s.d];
+            J.tab_cap = rdir[s.d] ? s.new_cap : x.tab_cap[s.d];
             J.ge_off = s.ge;
             J.dir = s.d;
             J.n = x.n;
             J.k = x.k;
             J.inst = s.id;
             cand += round_up(s.nc, kScanBlock);
-            if (reduce) {
+            if (rdir[s.d]) {
                 fills.push_back({s.new_tab, s.new_cap});
                 maxfill = std::max(maxfill, s.new_cap);
             } else if (s.new_tab >= 0) {
@@ -1069,9 +1079,15 @@ struct Engine {
         MarkJob *d_mark = nullptr;
         int64_t *d_mark_nt = nullptr;
         int n_mark = 0;
-        if (reduce) {
+        // the two-phase flags (winners, marks, survivors) are needed when
+        // any job of this iteration expands a reduced side; the other jobs
+        // get no marks, so phase 2 counts exactly their winners
+        bool marking = false;
+        for (const Sel &sl : sel) marking |= rdir[sl.d];
+        if (marking) {
             size_t cnt = 0;
-            for (const Sel &sl : sel) cnt += I[sl.id].lev[sl.d].size() + 1;
+            for (const Sel &sl : sel)
+                if (rdir[sl.d]) cnt += I[sl.id].lev[sl.d].size() + 1;
             MarkJob *mk = stg.take<MarkJob>(std::max<size_t>(cnt, 1), &d_mark);
             int64_t *nt = stg.take<int64_t>(2, &d_mark_nt);
             if (!stg.ok) return SW_EINTERNAL;
@@ -1096,6 +1112,7 @@ struct Engine {
             };
             for (int t = 0; t < nj; ++t) {
                 const Sel &sl = sel[t];
+                if (!rdir[sl.d]) continue;
                 const Inst &x = I[sl.id];
                 const int64_t co = jobs[t].cand_off, cn = sl.nc;
                 if (sl.d == 0) {
@@ -1157,27 +1174,27 @@ struct Engine {
         g_stats.candidates += ncand;
         if (!fills.empty()) CK(ops.fill(d_fill, (int)fills.size(), maxfill, L, st));
         if (!segs.empty()) CK(ops.rehash(d_segs, (int)segs.size(), rehash_total, L, st));
-        if (reduce) CK(cudaMemsetAsync(L.pairs + 3, 0, 3 * sizeof(unsigned long long), st));
+        if (marking) CK(cudaMemsetAsync(L.pairs + 3, 0, 3 * sizeof(unsigned long long), st));
         if (g_timing) CK(cudaEventRecord(g_ev.ev[0], st));
         CK(ops.expand(d_jobs, nj, ncand, L, st));
         if (g_timing) CK(cudaEventRecord(g_ev.ev[1], st));
-        if (reduce) {
+        if (marking) {
             CK(ops.mark(d_jobs, nj, ncand, d_mark, n_mark, d_mark_nt, mc, L, st));
             if (g_timing) CK(cudaEventRecord(g_ev.ev[7], st));
         }
-        CK(ops.compact(d_jobs, nj, ncand, reduce ? 2 : 0, L, st));
+        CK(ops.compact(d_jobs, nj, ncand, marking ? 2 : 0, L, st));
         if (g_timing) CK(cudaEventRecord(g_ev.ev[2], st));
         // the new levels' sizes and the status come back before the meet
         uint64_t *down = (uint64_t *)g_down.get((2 * nj + 8) * sizeof(uint64_t));
         if (!down) return SW_ECUDA;
         uint64_t *d_status = down + nj, *d_best = down + nj + 1, *d_pairs = down + 2 * nj + 1;
         uint64_t *d_mark_cnt = down + 2 * nj + 4;
-        if (reduce) d_mark_cnt[0] = d_mark_cnt[1] = d_mark_cnt[2] = 0;
+        if (marking) d_mark_cnt[0] = d_mark_cnt[1] = d_mark_cnt[2] = 0;
         CK(cudaMemcpyAsync(down, L.counts, nj * sizeof(uint64_t), cudaMemcpyDeviceToHost, st));
         CK(cudaMemcpyAsync(d_status, L.status, sizeof(uint32_t), cudaMemcpyDeviceToHost, st));
         if (counts_event) CK(cudaEventRecord(ev_counts, st));
         CK(cudaMemsetAsync(L.best, 0xFF, nj * sizeof(unsigned long long), st));
-        if (reduce) CK(cudaMemcpyAsync(d_mark_cnt, L.pairs + 3, 3 * sizeof(unsigned long long),
+        if (marking) CK(cudaMemcpyAsync(d_mark_cnt, L.pairs + 3, 3 * sizeof(unsigned long long),
                                        cudaMemcpyDeviceToHost, st));
         CK(cudaMemsetAsync(L.pairs, 0, 3 * sizeof(unsigned long long), st));
         if (g_timing) CK(cudaEventRecord(g_ev.ev[3], st));
@@ -1236,7 +1253,7 @@ struct Engine {
         CK(wait_stream(st));
         if (g_timing) {
             g_stats.expand_ms += elapsed(g_ev.ev[0], g_ev.ev[1]);
-            if (reduce) {
+            if (marking) {
                 g_stats.mark_ms += elapsed(g_ev.ev[1], g_ev.ev[7]);
                 g_stats.compact_ms += elapsed(g_ev.ev[7], g_ev.ev[2]);
             } else {
@@ -1244,13 +1261,14 @@ struct Engine {
             }
             g_stats.meet_ms += elapsed(g_ev.ev[3], g_ev.ev[4]);
         }
-        if (reduce) {
+        if (marking) {
             g_stats.mark_steps += (int64_t)d_mark_cnt[0];
             g_stats.mark_rows += (int64_t)d_mark_cnt[1];
             g_stats.mark_pairs += (int64_t)d_mark_cnt[2];
-            // this iteration's deduplication tables are done with
-            for (const Sel &sl : sel) tab_pool.release(sl.new_tab, sl.new_cap);
         }
+        // this iteration's deduplication tables of reduced sides are done with
+        for (const Sel &sl : sel)
+            if (rdir[sl.d]) tab_pool.release(sl.new_tab, sl.new_cap);
         g_stats.pairs += (int64_t)d_pairs[0];
         g_stats.and_iters += (int64_t)d_pairs[1];
         g_stats.rows_transposed += (int64_t)d_pairs[2];
@@ -1270,7 +1288,7 @@ struct Engine {
                                      [&](const Sel &s) {
                                          if (I[s.id].state == kActive) return false;
                                          planned[s.id] = 0;
-                                         if (reduce) tab_pool.release(s.new_tab, s.new_cap);
+                                         if (rdir[s.d]) tab_pool.release(s.new_tab, s.new_cap);
                                          return true;
                                      }),
                       pending.end());
@@ -1925,7 +1943,7 @@ void sw_set_options(const sw_options *opt) {
     if (g_opt.meet_algo != 1) g_opt.meet_algo = 0;
     if (g_opt.meet_f_rows < 0) g_opt.meet_f_rows = 0;
     if (g_opt.meet_lane_words != 4) g_opt.meet_lane_words = 0;
-    if (g_opt.reduce != 1) g_opt.reduce = 0;
+    if (g_opt.reduce < 0 || g_opt.reduce > 3) g_opt.reduce = 0;
     if (g_opt.table_cap_slots < 0) g_opt.table_cap_slots = 0;
 }
 

@@ -1006,27 +1006,31 @@ __global__ void __launch_bounds__(NT) k_meet_bm(const MeetJob *__restrict__ jobs
                 struct Frag {
                     uint32_t w[2 * LW];
                 };
-                auto load_frag = [&](int q, bool on) {
-                    Frag fr;
+                // loads the lane's words of state q's bitmap into fr; a lane
+                // with `on` false keeps fr's old words (its intersection is
+                // already all zero, so they change nothing), which spares
+                // the zeroing
+                auto load_into = [&](Frag &fr, int q, bool on) {
                     const uint32_t *row = lbase + q * G::kStride;
 #pragma unroll
                     for (int h = 0; h < G::UPL; ++h) {
                         const uint32_t *p = row + 32 * h * G::U;
                         if constexpr (G::U == 4) {
-                            uint4 v = make_uint4(0, 0, 0, 0);
-                            if (on) v = *reinterpret_cast<const uint4 *>(p);
-                            fr.w[4 * h] = v.x;
-                            fr.w[4 * h + 1] = v.y;
-                            fr.w[4 * h + 2] = v.z;
-                            fr.w[4 * h + 3] = v.w;
+                            if (on) {
+                                const uint4 v = *reinterpret_cast<const uint4 *>(p);
+                                fr.w[4 * h] = v.x;
+                                fr.w[4 * h + 1] = v.y;
+                                fr.w[4 * h + 2] = v.z;
+                                fr.w[4 * h + 3] = v.w;
+                            }
                         } else {
-                            uint2 v = make_uint2(0, 0);
-                            if (on) v = *reinterpret_cast<const uint2 *>(p);
-                            fr.w[2 * h] = v.x;
-                            fr.w[2 * h + 1] = v.y;
+                            if (on) {
+                                const uint2 v = *reinterpret_cast<const uint2 *>(p);
+                                fr.w[2 * h] = v.x;
+                                fr.w[2 * h + 1] = v.y;
+                            }
                         }
                     }
-                    return fr;
                 };
                 auto and2 = [&](const Frag &x, const Frag &y) {
 #pragma unroll
@@ -1048,28 +1052,28 @@ __global__ void __launch_bounds__(NT) k_meet_bm(const MeetJob *__restrict__ jobs
                 const int s6 = (int)(r.w & 0xFFFFu);
                 uint32_t steps = 4;
                 bool la, alive;
-                {
-                    const Frag a0 = load_frag(s0, true), b0 = load_frag(s1, true);
-                    const Frag a1 = load_frag(s2, true), b1 = load_frag(s3, true);
-                    and2(a0, b0);
-                    and2(a1, b1);
-                }
+                Frag fa0, fb0, fa1, fb1;
+                load_into(fa0, s0, true);
+                load_into(fb0, s1, true);
+                load_into(fa1, s2, true);
+                load_into(fb1, s3, true);
+                and2(fa0, fb0);
+                and2(fa1, fb1);
                 la = lane_alive();
-                {
-                    const Frag a2 = load_frag(s4, la), b2 = load_frag(s5, la);
+                load_into(fa0, s4, la);
+                load_into(fb0, s5, la);
+                alive = __any_sync(0xffffffffu, la);
+                if (alive) {
+                    steps = 6;
+                    and2(fa0, fb0);
+                    la = lane_alive();
+                    load_into(fa1, s6, la);
                     alive = __any_sync(0xffffffffu, la);
                     if (alive) {
-                        steps = 6;
-                        and2(a2, b2);
+                        steps = 7;
+                        and1(fa1);
                         la = lane_alive();
-                        const Frag a3 = load_frag(s6, la);
                         alive = __any_sync(0xffffffffu, la);
-                        if (alive) {
-                            steps = 7;
-                            and1(a3);
-                            la = lane_alive();
-                            alive = __any_sync(0xffffffffu, la);
-                        }
                     }
                 }
                 if (alive && card > 7) {
@@ -1085,7 +1089,8 @@ __global__ void __launch_bounds__(NT) k_meet_bm(const MeetJob *__restrict__ jobs
                         while (bits && alive) {
                             const int q = lo + __ffs(bits) - 1;
                             bits &= bits - 1;
-                            and1(load_frag(q, la));
+                            load_into(fa0, q, la);
+                            and1(fa0);
                             la = lane_alive();
                             alive = __any_sync(0xffffffffu, la);
                             ++steps;
@@ -1295,28 +1300,33 @@ __global__ void __launch_bounds__(NT) k_mark_bm(const MarkJob *__restrict__ jobs
             struct Frag {
                 uint32_t w[NWORD];
             };
-            auto load_frag = [&](int q, bool on) {
-                Frag fr;
+            // as in the meet kernel: a lane with `on` false keeps fr's old
+            // words (its intersection is already zero)
+            auto load_into = [&](Frag &fr, int q, bool on) {
                 const uint32_t *rowp = lbase + q * G::kStride;
 #pragma unroll
                 for (int h = 0; h < G::UPL; ++h) {
                     const uint32_t *p = rowp + 32 * h * G::U;
                     if constexpr (G::U == 4) {
-                        uint4 v = make_uint4(0, 0, 0, 0);
-                        if (on) v = *reinterpret_cast<const uint4 *>(p);
-                        fr.w[4 * h] = v.x;
-                        fr.w[4 * h + 1] = v.y;
-                        fr.w[4 * h + 2] = v.z;
-                        fr.w[4 * h + 3] = v.w;
+                        if (on) {
+                            const uint4 v = *reinterpret_cast<const uint4 *>(p);
+                            fr.w[4 * h] = v.x;
+                            fr.w[4 * h + 1] = v.y;
+                            fr.w[4 * h + 2] = v.z;
+                            fr.w[4 * h + 3] = v.w;
+                        }
                     } else {
-                        uint2 v = make_uint2(0, 0);
-                        if (on) v = *reinterpret_cast<const uint2 *>(p);
-                        fr.w[2 * h] = v.x;
-                        fr.w[2 * h + 1] = v.y;
+                        if (on) {
+                            const uint2 v = *reinterpret_cast<const uint2 *>(p);
+                            fr.w[2 * h] = v.x;
+                            fr.w[2 * h + 1] = v.y;
+                        }
                     }
                 }
-                return fr;
             };
+            Frag fa, fb;
+#pragma unroll
+            for (int j = 0; j < NWORD; ++j) fa.w[j] = fb.w[j] = 0;
             bool la = true, alive = true;
             int walked = 0, pend = -1;
             // the row's states in increasing order, ANDed two at a time
@@ -1330,9 +1340,10 @@ __global__ void __launch_bounds__(NT) k_mark_bm(const MarkJob *__restrict__ jobs
                         pend = q;
                         continue;
                     }
-                    const Frag a = load_frag(pend, la), b = load_frag(q, la);
+                    load_into(fa, pend, la);
+                    load_into(fb, q, la);
 #pragma unroll
-                    for (int j = 0; j < NWORD; ++j) acc[j] &= a.w[j] & b.w[j];
+                    for (int j = 0; j < NWORD; ++j) acc[j] &= fa.w[j] & fb.w[j];
                     pend = -1;
                     walked += 2;
                     if (walked >= 4) {
@@ -1345,9 +1356,9 @@ __global__ void __launch_bounds__(NT) k_mark_bm(const MarkJob *__restrict__ jobs
                 }
             }
             if (alive && pend >= 0) {
-                const Frag a = load_frag(pend, la);
+                load_into(fa, pend, la);
 #pragma unroll
-                for (int j = 0; j < NWORD; ++j) acc[j] &= a.w[j];
+                for (int j = 0; j < NWORD; ++j) acc[j] &= fa.w[j];
                 ++walked;
             }
             if (alive) {

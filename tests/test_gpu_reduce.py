@@ -1,6 +1,7 @@
-"""GPU search with the inclusion reductions of Alg. 1 (sw_options.reduce = 1)
-against the CPU oracle's restatement (oracle.bidir_reduced,
-oracle.reduced_level_sizes), element by element, through the C-ABI.
+"""GPU search with the inclusion reductions of Alg. 1 (sw_options.reduce = 1:
+both sides; 2: the BFS side; 3: the IBFS side) against the CPU oracle's
+restatement (oracle.bidir_reduced with the same sides), element by
+element, through the C-ABI.
 
 r and every computed reduced level size must be identical.  The word of
 the reduced search depends on the forward depth at which the two searches
@@ -36,13 +37,16 @@ def ws(sw):
     return sw.workspace(512 << 20)
 
 
-@pytest.fixture
-def reduced(sw):
+SIDES = {1: 3, 2: 1, 3: 2}  # sw_options.reduce -> the oracle's side mask
+
+
+@pytest.fixture(params=[1, 2, 3], ids=["both", "bfs", "ibfs"])
+def reduced(sw, request):
     old = sw.sw_get_options()
     o = sw.sw_get_options()
-    o.reduce = 1
+    o.reduce = request.param
     sw.sw_set_options(o)
-    yield
+    yield SIDES[request.param]
     sw.sw_set_options(old)
 
 
@@ -53,14 +57,13 @@ def resets(delta, word):
     return len(np.unique(states)) == 1
 
 
-def check(sw, d, h, r, w):
+def check(sw, d, h, r, w, dirs):
     fs, bs = sw.sw_level_sizes(h)
     i = len(fs) - 1
-    ro, wo, fo, bo = oracle.bidir_reduced(d, fwd_depth=i)
+    ro, wo, fo, bo = oracle.bidir_reduced(d, fwd_depth=i, dirs=dirs)
     assert r == ro and len(fs) + len(bs) - 2 == r
     assert w == wo and resets(d, w)
-    assert fs == fo
-    assert bs == oracle.reduced_level_sizes(d, 1, len(bs) - 1)
+    assert fs == fo and bs == bo
 
 
 def test_hand_examples(sw, ws, reduced):
@@ -69,7 +72,7 @@ def test_hand_examples(sw, ws, reduced):
         h = sw.load(d)
         r, w = sw.sw_reset_threshold(h, ws=ws)
         assert r == ex["r"], ex["name"]
-        check(sw, d, h, r, w)
+        check(sw, d, h, r, w, reduced)
 
 
 @pytest.mark.parametrize("n", list(range(1, 21)))
@@ -78,7 +81,7 @@ def test_cerny(sw, ws, reduced, n):
     h = sw.load(d)
     r, w = sw.sw_reset_threshold(h, ws=ws)
     assert r == (n - 1) ** 2
-    check(sw, d, h, r, w)
+    check(sw, d, h, r, w, reduced)
 
 
 def _random_cases():
@@ -97,7 +100,7 @@ def test_random_vs_oracle(sw, ws, reduced, n, k, seed):
     h = sw.load(d)
     r, w = sw.sw_reset_threshold(h, ws=ws)
     assert r == oracle.bidir(d)[0]
-    check(sw, d, h, r, w)
+    check(sw, d, h, r, w, reduced)
 
 
 @pytest.mark.parametrize("n,m,k,seed", [(250, 40, 3, 4), (330, 48, 2, 7), (450, 50, 2, 5), (576, 44, 2, 3)])
@@ -106,7 +109,7 @@ def test_wide_sets_vs_oracle(sw, ws, reduced, n, m, k, seed):
     d = gen.core_automaton(n, m, k, seed)
     h = sw.load(d)
     r, w = sw.sw_reset_threshold(h, ws=ws)
-    check(sw, d, h, r, w)
+    check(sw, d, h, r, w, reduced)
 
 
 def test_max_letters(sw, ws, reduced):
@@ -114,7 +117,7 @@ def test_max_letters(sw, ws, reduced):
         d = gen.random_automaton(n, sw.SW_MAX_LETTERS, seed)
         h = sw.load(d)
         r, w = sw.sw_reset_threshold(h, ws=ws)
-        check(sw, d, h, r, w)
+        check(sw, d, h, r, w, reduced)
 
 
 def test_ragged_batch(sw, ws, reduced):
@@ -129,7 +132,7 @@ def test_ragged_batch(sw, ws, reduced):
     hs = [sw.load(d) for d in ds]
     rb, wb = sw.sw_batch(hs, ws=ws)
     for i, d in enumerate(ds):
-        check(sw, d, hs[i], int(rb[i]), wb[i])
+        check(sw, d, hs[i], int(rb[i]), wb[i], reduced)
 
 
 @functools.lru_cache(maxsize=None)
@@ -153,8 +156,10 @@ def test_c3_sample_reduced_r_and_sizes(sw, reduced):
         assert len(wb[i]) == it["r"] and resets(ds[i], wb[i])
         if ds[i].shape[1] <= 90:
             fs, bs = sw.sw_level_sizes(hs[i])
-            assert fs == oracle.reduced_level_sizes(ds[i], 0, len(fs) - 1)
-            assert bs == oracle.reduced_level_sizes(ds[i], 1, len(bs) - 1)
+            side = lambda dr, depth: (oracle.reduced_level_sizes if reduced & (1 << dr)  # noqa: E731
+                                      else oracle.level_sizes)(ds[i], dr, depth)
+            assert fs == side(0, len(fs) - 1)
+            assert bs == side(1, len(bs) - 1)
 
 
 def test_reduced_equals_plain_r_in_waves(sw, reduced):
