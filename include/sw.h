@@ -281,6 +281,14 @@ int32_t sw_last_reduce_stats(double *mark_ms, int64_t *mark_pairs, int64_t *mark
  */
 int32_t sw_probe_int_peak(void *stream, void *workspace, size_t ws_bytes, double *lop3_per_clk_per_sm);
 
+/*
+ * ExpMark(As, Bs, Ad, Bd) of Section 2.1.2: the expected number of subset
+ * checks of MarkSupersets over lists of As and Bs sets with densities Ad
+ * and Bd (density = summed cardinality / (n * sets)), as the direction rule
+ * dir_rule = 1 uses it.  Densities are clamped into (0, 1).  Host only.
+ */
+double sw_expmark(double a_s, double b_s, double a_d, double b_d);
+
 /* Enables (1) or disables (0) per-kernel CUDA-event timing for later
  * searches on the calling thread. */
 void sw_set_timing(int32_t on);
@@ -331,6 +339,12 @@ void sw_set_timing(int32_t on);
  *                         no longer take its sets fails alone with
  *                         SW_ENOMEM (its result r = -1 in a batch) while
  *                         the other instances of the call go on.
+ *   dir_rule:             the meet term of the step costs (Section 2.1.2):
+ *                         0 (default) the pair tests left after duplicates,
+ *                         k (1 - r_dupl) |L| |other|; 1 the paper's ExpMark
+ *                         estimate with the lists' densities (eq. 1 and 4).
+ *                         The schedule never changes r, the word or the
+ *                         level sizes.
  * Applies to later searches on the calling thread.
  */
 typedef struct sw_options {
@@ -343,6 +357,7 @@ typedef struct sw_options {
     double set_cost;
     int32_t reduce;
     int32_t table_cap_slots;
+    int32_t dir_rule;
 } sw_options;
 
 void sw_get_options(sw_options *opt);

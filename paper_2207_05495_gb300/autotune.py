@@ -2,9 +2,12 @@
 
 It times the batched search on a sample of automata for every candidate
 setting of the meet kernel's forward rows per tile and backward chunk size
-(lane words), and of the direction rule (SetCost and the threshold theta of
-the step-cost comparison, Section 2.1.2), requires every candidate to
-return identical r and words, and keeps the fastest.  Results are cached in tuned.json next to this file,
+(lane words), of the direction rule (SetCost, the threshold theta of the
+step-cost comparison and its meet term, pair count or ExpMark, Section
+2.1.2), and of the inclusion reductions (none, or the BFS side's, Alg. 1),
+requires every candidate to return identical r (and identical words among
+candidates with the same reductions: a reduced BFS side returns another
+shortest word), and keeps the fastest.  Results are cached in tuned.json next to this file,
 keyed by (words per set W, letters k, GPU name); `apply` loads the entry for
 a workload into the calling thread's options.
 
@@ -25,10 +28,12 @@ from . import gen, sw
 CACHE = os.path.join(os.path.dirname(os.path.abspath(__file__)), "tuned.json")
 
 GRID = {
-    "meet_f_rows": [1024, 4096, 16384],
+    "meet_f_rows": [4096, 16384],
     "meet_lane_words": [0, 4],
-    "set_cost": [8192.0, 32768.0, 131072.0],
+    "set_cost": [512.0, 8192.0, 131072.0],
     "dir_theta": [0.5, 1.0, 2.0],
+    "reduce": [0, 2],
+    "dir_rule": [0, 1],
 }
 
 
@@ -49,7 +54,8 @@ def tune(automata, ws, grid=None, repeats: int = 2, verbose: bool = False) -> di
     hs = [sw.load(d) for d in automata]
     base = sw.sw_get_options()
     names = list(grid)
-    ref = None
+    ref_r = None
+    ref_words = {}  # per reduction setting
     trials = []
     try:
         for combo in itertools.product(*(grid[n] for n in names)):
@@ -66,9 +72,12 @@ def tune(automata, ws, grid=None, repeats: int = 2, verbose: bool = False) -> di
                 torch.cuda.synchronize()
                 t = time.perf_counter() - t0
                 best_t = t if best_t is None else min(best_t, t)
-            if ref is None:
-                ref = (r.copy(), w)
-            elif not ((r == ref[0]).all() and w == ref[1]):
+            red = int(getattr(o, "reduce", 0))
+            if ref_r is None:
+                ref_r = r.copy()
+            if red not in ref_words:
+                ref_words[red] = w
+            if not ((r == ref_r).all() and w == ref_words[red]):
                 raise RuntimeError(f"setting {dict(zip(names, combo))} changed the results")
             trial = dict(zip(names, combo))
             trial["seconds"] = best_t

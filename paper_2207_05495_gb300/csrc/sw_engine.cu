@@ -58,7 +58,7 @@ struct Stats {
 };
 
 thread_local int32_t g_last_error = SW_OK;
-thread_local sw_options g_opt = {0, 0, 0, 4096, 0, 1.0, 8192.0, 0, 0};
+thread_local sw_options g_opt = {0, 0, 0, 4096, 0, 1.0, 8192.0, 0, 0, 0};
 thread_local bool g_timing = false;
 thread_local Stats g_stats;
 // Set only while sw_reset_threshold_static runs: staging buffers then come
@@ -217,6 +217,7 @@ struct Inst {
     std::vector<Chunk> chunks;
     int64_t tab_off[2] = {-1, -1}, tab_cap[2] = {0, 0}, stored[2] = {0, 0};
     double dupl[2] = {0.0, 0.0};
+    double dens[2] = {1.0, 0.0};  // density (Section 2.1.2) of the last level of each side
     int32_t state = kWaiting, code = SW_OK, r = -1;
     int32_t evictions = 0;
     int64_t word_off = 0, word_cap = 0;    // where the word goes
@@ -235,7 +236,8 @@ struct Layout {
     // staging mirror for per-iteration job uploads (one H2D copy per phase)
     char *mirror;
     size_t mirror_bytes;
-    uint64_t *counts;  // per-job survivors
+    uint64_t *counts;    // per-job survivors
+    uint64_t *card_sum;  // per-job summed cardinality of the new level
     int64_t *ntiles;   // meet tiles of the current iteration, then the bitmap kernel's tile counter
     unsigned long long *best;
     uint32_t *word_status;
@@ -294,6 +296,7 @@ size_t small_area_bytes(int32_t count, int64_t delta_elems, int W = 9) {
     auto add = [&](size_t x) { b += (x + 255) & ~(size_t)255; };
     add(mirror_bytes_for(count));
     add(c * sizeof(uint64_t));
+    add(c * sizeof(uint64_t));
     add(2 * sizeof(int64_t));
     add(c * sizeof(unsigned long long));
     add(c * sizeof(uint32_t));
@@ -314,6 +317,7 @@ bool carve(void *ws, size_t bytes, int W, int32_t count, int64_t delta_elems, La
     L.mirror_bytes = mirror_bytes_for(count);
     L.mirror = cv.take<char>(L.mirror_bytes);
     L.counts = cv.take<uint64_t>(c);
+    L.card_sum = cv.take<uint64_t>(c);
     L.ntiles = cv.take<int64_t>(2);
     L.best = cv.take<unsigned long long>(c);
     L.word_status = cv.take<uint32_t>(c);
@@ -495,7 +499,7 @@ cudaError_t launch_mark_bm(const MarkJob *jobs, int njobs, int64_t *ntiles, int 
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, NT, smem);
     int64_t grid = (int64_t)sm_count() * std::max(per_sm, 1);
     kern<<<(unsigned)grid, NT, smem, st>>>(jobs, njobs, ntiles, tr_rows, n_cap, L.sets, L.cand_sets, L.flag, L.meta,
-                                           L.pairs + 3);
+                                           L.perm, L.pairs + 3);
     return cudaGetLastError();
 }
 
@@ -551,7 +555,7 @@ struct Ops {
         k_flag_count<W><<<(unsigned)nblocks, kScanThreads, 0, st>>>(jobs, nj, ncand, L.cand_slot, L.table,
                                                                     L.cand_sets, L.flag, L.block_cnt, L.hist, phase);
         k_scan_blocks<<<1, 1024, 0, st>>>(nblocks, L.block_cnt, L.block_off);
-        k_ge<<<(unsigned)nj, 32, 0, st>>>(jobs, HN, L.hist, L.cursor, L.meta);
+        k_ge<<<(unsigned)nj, 32, 0, st>>>(jobs, HN, L.hist, L.cursor, L.meta, L.card_sum);
         k_compact<W><<<(unsigned)nblocks, kScanThreads, 0, st>>>(jobs, nj, ncand, L.flag, L.block_off, L.cand_sets,
                                                                  L.cand_slot, L.table, L.sets, L.link, L.perm,
                                                                  L.rec, L.cursor);
@@ -578,10 +582,12 @@ struct Ops {
         k_meet_prep<<<1, 1024, 0, st>>>(jobs, nj, L.counts, TF, c.tb, L.ntiles);
         int64_t *ntiles = L.ntiles;
         if (c.algo == 0) {
+            // 8192-set chunks: one CTA per SM (200 KB of bitmaps at 192
+            // states); 512 threads keep the walk's registers from spilling
             if constexpr (W <= 3)
                 if (c.lw == 4)
-                    return launch_meet_bm<W, 4, 1024>(jobs, nj, ntiles, tf_rows, c.n_cap, L.sets, L.perm, L.rec,
-                                                      L.best, L.pairs, L.pairs + 1, L.pairs + 2, L.meta, st);
+                    return launch_meet_bm<W, 4, 512>(jobs, nj, ntiles, tf_rows, c.n_cap, L.sets, L.perm, L.rec,
+                                                     L.best, L.pairs, L.pairs + 1, L.pairs + 2, L.meta, st);
             if constexpr (W >= 4 && W <= 7)
                 if (c.lw == 2)
                     return launch_meet_bm<W, 2, 1024>(jobs, nj, ntiles, tf_rows, c.n_cap, L.sets, L.perm, L.rec,
@@ -696,6 +702,23 @@ cudaError_t wait_stream(cudaStream_t st) {
     return e;
 }
 
+// ---------------------------------------------------------------- cost estimate
+
+// ExpMark (Section 2.1.2): the expected number of subset checks of
+// MarkSupersets(A, B) for lists of As and Bs sets of densities Ad and Bd,
+// Bs ((1 + Bd) / Bd + 1 / (Ad - Ad Bd)) As^(log_w (1 + Bd)) with
+// w = (1 + Bd) / (1 + Ad Bd - Ad).  Densities are clamped into (0, 1), where
+// the formula is defined.
+double expmark(double As, double Bs, double Ad, double Bd) {
+    if (As <= 0 || Bs <= 0) return 0.0;
+    const double lo = 1e-6, hi = 1.0 - 1e-6;
+    Ad = std::min(std::max(Ad, lo), hi);
+    Bd = std::min(std::max(Bd, lo), hi);
+    const double w = (1.0 + Bd) / (1.0 + Ad * Bd - Ad);
+    const double e = std::log1p(Bd) / std::log(w);
+    return Bs * ((1.0 + Bd) / Bd + 1.0 / (Ad - Ad * Bd)) * std::pow(As, e);
+}
+
 // ---------------------------------------------------------------- the search engine
 
 // Runs instances (state kWaiting, in `queue`) to completion.  Memory of an
@@ -795,10 +818,22 @@ struct Engine {
         return SW_OK;
     }
 
+    // The step-cost comparison of Section 2.1.2 (its one-step greedy rule):
+    // the cost of a step is SetCost * k * |L| for making the sets plus the
+    // cost of the meet check that follows.  dir_rule 0 counts the meet as
+    // the pair tests left after duplicates, k (1 - r_dupl) |L| |other|;
+    // dir_rule 1 estimates it with ExpMark (eq. 1 and 4, with the lists'
+    // densities).  The side with the smaller cost (up to dir_theta) steps.
     int choose_dir(const Inst &x) const {
         double F = (double)x.lev[0].back().cnt, B = (double)x.lev[1].back().cnt, k = x.k;
-        double cF = g_opt.set_cost * k * F + k * (1.0 - x.dupl[0]) * F * B;
-        double cB = g_opt.set_cost * k * B + k * (1.0 - x.dupl[1]) * B * F;
+        double cF, cB;
+        if (g_opt.dir_rule == 1) {
+            cF = g_opt.set_cost * k * F + expmark(k * (1.0 - x.dupl[0]) * F, B, x.dens[0], x.dens[1]);
+            cB = g_opt.set_cost * k * B + expmark(F, k * (1.0 - x.dupl[1]) * B, x.dens[0], x.dens[1]);
+        } else {
+            cF = g_opt.set_cost * k * F + k * (1.0 - x.dupl[0]) * F * B;
+            cB = g_opt.set_cost * k * B + k * (1.0 - x.dupl[1]) * B * F;
+        }
         return cF <= g_opt.dir_theta * cB ? 0 : 1;
     }
 
@@ -848,6 +883,8 @@ struct Engine {
                 x.lev[d].clear();
                 x.dupl[d] = 0.0;
             }
+            x.dens[0] = 1.0;                 // Q
+            x.dens[1] = 1.0 / (double)x.n;   // the singletons
             x.lev[0].push_back({f, 1, 1, -1});
             x.lev[1].push_back({b, x.n, x.n, -1});
             x.tab_off[0] = t0;
@@ -1094,7 +1131,7 @@ struct Engine {
             const int64_t kr = (int64_t)2048 * (mc.lw == 4 ? bm_lanes_words(W) : mc.lw);  // chunk rows
             int64_t tiles = 0;
             auto add = [&](int64_t r_off, int64_t r_cnt, int r_cand, int64_t c_off, int64_t c_cnt, int c_cand,
-                           int64_t ge, int col, int self) {
+                           int64_t ge, int col, int self, int r_perm) {
                 if (r_cnt <= 0 || c_cnt <= 0) return;
                 MarkJob &M = mk[n_mark++];
                 M.tile_off = tiles;
@@ -1108,6 +1145,8 @@ struct Engine {
                 M.c_cand = c_cand;
                 M.col = col;
                 M.self = self;
+                M.r_perm = r_perm;
+                M.pad = 0;
                 tiles += ((r_cnt + kMarkRows - 1) / kMarkRows) * M.ntc;
             };
             for (int t = 0; t < nj; ++t) {
@@ -1116,11 +1155,12 @@ struct Engine {
                 const Inst &x = I[sl.id];
                 const int64_t co = jobs[t].cand_off, cn = sl.nc;
                 if (sl.d == 0) {
-                    add(co, cn, 1, co, cn, 1, -1, 1, 1);
-                    for (const Level &l : x.lev[0]) add(l.off, l.cnt, 0, co, cn, 1, -1, 1, 0);
+                    add(co, cn, 1, co, cn, 1, -1, 1, 1, 0);
+                    // a forward level's permutation lists its sets by increasing cardinality
+                    for (const Level &l : x.lev[0]) add(l.off, l.cnt, 0, co, cn, 1, -1, 1, 0, 1);
                 } else {
-                    add(co, cn, 1, co, cn, 1, -1, 0, 1);
-                    for (const Level &l : x.lev[1]) add(co, cn, 1, l.off, l.cnt, 0, l.ge, 0, 0);
+                    add(co, cn, 1, co, cn, 1, -1, 0, 1, 0);
+                    for (const Level &l : x.lev[1]) add(co, cn, 1, l.off, l.cnt, 0, l.ge, 0, 0, 0);
                 }
             }
             nt[0] = tiles;
@@ -1185,13 +1225,15 @@ struct Engine {
         CK(ops.compact(d_jobs, nj, ncand, marking ? 2 : 0, L, st));
         if (g_timing) CK(cudaEventRecord(g_ev.ev[2], st));
         // the new levels' sizes and the status come back before the meet
-        uint64_t *down = (uint64_t *)g_down.get((2 * nj + 8) * sizeof(uint64_t));
+        uint64_t *down = (uint64_t *)g_down.get((3 * nj + 8) * sizeof(uint64_t));
         if (!down) return SW_ECUDA;
         uint64_t *d_status = down + nj, *d_best = down + nj + 1, *d_pairs = down + 2 * nj + 1;
         uint64_t *d_mark_cnt = down + 2 * nj + 4;
+        uint64_t *d_card_sum = down + 2 * nj + 8;
         if (marking) d_mark_cnt[0] = d_mark_cnt[1] = d_mark_cnt[2] = 0;
         CK(cudaMemcpyAsync(down, L.counts, nj * sizeof(uint64_t), cudaMemcpyDeviceToHost, st));
         CK(cudaMemcpyAsync(d_status, L.status, sizeof(uint32_t), cudaMemcpyDeviceToHost, st));
+        CK(cudaMemcpyAsync(d_card_sum, L.card_sum, nj * sizeof(uint64_t), cudaMemcpyDeviceToHost, st));
         if (counts_event) CK(cudaEventRecord(ev_counts, st));
         CK(cudaMemsetAsync(L.best, 0xFF, nj * sizeof(unsigned long long), st));
         if (marking) CK(cudaMemcpyAsync(d_mark_cnt, L.pairs + 3, 3 * sizeof(unsigned long long),
@@ -1239,6 +1281,7 @@ struct Engine {
             inst_shrink(x, s.dest, s.nc, c);
             x.lev[s.d].push_back({s.dest, c, c, s.ge});
             x.dupl[s.d] = 1.0 - (double)c / (double)s.nc;
+            if (c > 0) x.dens[s.d] = (double)d_card_sum[t] / ((double)x.n * (double)c);
             x.stored[s.d] += c;
             if (c == 0) finish(x, kFailed, SW_ENOTSYNC);
         }
@@ -1945,7 +1988,10 @@ void sw_set_options(const sw_options *opt) {
     if (g_opt.meet_lane_words != 4) g_opt.meet_lane_words = 0;
     if (g_opt.reduce < 0 || g_opt.reduce > 3) g_opt.reduce = 0;
     if (g_opt.table_cap_slots < 0) g_opt.table_cap_slots = 0;
+    if (g_opt.dir_rule != 1) g_opt.dir_rule = 0;
 }
+
+double sw_expmark(double a_s, double b_s, double a_d, double b_d) { return expmark(a_s, b_s, a_d, b_d); }
 
 int32_t sw_last_reduce_stats(double *mark_ms, int64_t *mark_pairs, int64_t *mark_steps, int64_t *mark_rows) {
     if (mark_rows) *mark_rows = g_stats.mark_rows;

@@ -157,6 +157,28 @@ __device__ __forceinline__ uint64_t ld_relaxed(const uint64_t *p) {
     return v;
 }
 
+// Slot operations of the deduplication table with the memory ordering the
+// table needs and no more: a candidate's set is written, then its id is
+// published by a release CAS (or handed over by a release min), and a
+// thread that reads an id with acquire semantics sees the set written
+// before it was published.
+__device__ __forceinline__ uint64_t ld_acquire(const uint64_t *p) {
+    uint64_t v;
+    asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+    return v;
+}
+
+__device__ __forceinline__ uint64_t cas_acq_rel(uint64_t *p, uint64_t cmp, uint64_t val) {
+    uint64_t old;
+    asm volatile("atom.acq_rel.gpu.global.cas.b64 %0, [%1], %2, %3;" : "=l"(old) : "l"(p), "l"(cmp), "l"(val)
+                 : "memory");
+    return old;
+}
+
+__device__ __forceinline__ void min_release(uint64_t *p, uint64_t val) {
+    asm volatile("red.release.gpu.global.min.u64 [%0], %1;" ::"l"(p), "l"(val) : "memory");
+}
+
 __device__ __forceinline__ uint32_t ld_relaxed32(const uint32_t *p) {
     uint32_t v;
     asm volatile("ld.relaxed.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
@@ -422,26 +444,26 @@ __global__ void __launch_bounds__(256) k_expand(
         }
 #pragma unroll
         for (int w = 0; w < W; ++w) cand_sets[c * W + w] = T[w];
-        __threadfence();  // publish the set before its id can be seen in the table
+        // the set is published by the release CAS (or release min) below;
+        // reads of other candidates' sets follow an acquire of their ids
         const uint64_t me = kCand + (uint64_t)c;
         uint64_t pos = (uint64_t)J.tab_off + __umul64hi(hash_set<W>(dir, T), (uint64_t)J.tab_cap);
         int64_t result = -1;
         int probe = 0;
         for (; probe < kMaxProbe; ++probe) {
             uint64_t *slot = table + pos;
-            uint64_t v = ld_relaxed(slot);
+            uint64_t v = ld_acquire(slot);
             if (v == kEmpty) {
-                unsigned long long old = atomicCAS((unsigned long long *)slot, kEmpty, (unsigned long long)me);
+                const uint64_t old = cas_acq_rel(slot, kEmpty, me);
                 if (old == kEmpty) { result = (int64_t)pos; break; }
                 v = old;
             }
-            __threadfence();  // order the reads of v's set after observing v
             if (v < kCand) {  // a stored set (earlier level)
                 if (set_equal<W>(T, sets + v * W)) break;  // seen before: drop
             } else {
                 uint64_t c2 = v - kCand;
                 if (set_equal_cg<W>(T, cand_sets + c2 * W)) {
-                    atomicMin((unsigned long long *)slot, (unsigned long long)me);
+                    min_release(slot, me);
                     result = (int64_t)pos;
                     break;
                 }
@@ -528,12 +550,17 @@ __global__ void __launch_bounds__(kScanThreads) k_flag_count(
 // whose table ge[c] = sets with at least c states also goes to
 // meta[ge_off + c] (when the job has a table; ge_off = -1 when the table
 // pool was full); in increasing order for a forward job (its permutation).
+// card_sum[job] = the summed cardinality of the job's new level (its
+// density for the step-cost estimate of Section 2.1.2).
 __global__ void k_ge(const ExpandJob *__restrict__ jobs, int hn, const uint32_t *__restrict__ hist,
-                     uint32_t *__restrict__ cursor, int32_t *__restrict__ meta) {
+                     uint32_t *__restrict__ cursor, int32_t *__restrict__ meta, uint64_t *__restrict__ card_sum) {
     const ExpandJob &J = jobs[blockIdx.x];
     if (threadIdx.x != 0) return;
     const uint32_t *h = hist + (int64_t)blockIdx.x * hn;
     uint32_t *cur = cursor + (int64_t)blockIdx.x * hn;
+    uint64_t sum = 0;
+    for (int c = 0; c < hn; ++c) sum += (uint64_t)c * h[c];
+    card_sum[blockIdx.x] = sum;
     if (J.dir == 0) {
         uint32_t below = 0;  // sets with fewer than c states
         for (int c = 0; c < hn; ++c) {
@@ -1162,6 +1189,8 @@ struct MarkJob {
     int64_t c_off, c_cnt;      // chunk: candidate ids (c_cand) or arena indices
     int64_t ge_off;            // arena chunk sorted by decreasing cardinality: its ge table, or -1
     int32_t r_cand, c_cand, col, self;
+    int32_t r_perm;            // arena rows of a forward level, visited through its permutation
+    int32_t pad;               // (increasing cardinality), so a warp stops at its first row too large
 };
 
 // Inclusion marking by vertical bitmaps, as k_meet_bm: the chunk (up to
@@ -1178,6 +1207,7 @@ __global__ void __launch_bounds__(NT) k_mark_bm(const MarkJob *__restrict__ jobs
                                                 const uint64_t *__restrict__ sets,
                                                 const uint64_t *__restrict__ cand_sets, uint8_t *flag,
                                                 const int32_t *__restrict__ meta,
+                                                const uint32_t *__restrict__ perm,
                                                 unsigned long long *counters) {
     constexpr int HN = card_slots(W);
     using G = Bm<LW>;
@@ -1259,7 +1289,7 @@ __global__ void __launch_bounds__(NT) k_mark_bm(const MarkJob *__restrict__ jobs
         for (int j = 0; j < NWORD; ++j) hit[j] = 0;
         // 2. rows, one per warp at a time
         for (int64_t i = i0 + warp; maxcard >= 0 && i < i1; i += NW) {
-            const int64_t ridx = J.r_off + i;
+            const int64_t ridx = J.r_perm ? J.r_off + (int64_t)__ldg(perm + J.r_off + i) : J.r_off + i;
             if (J.r_cand) {
                 // lane 0 reads the flag; the warp follows its decision
                 int fl = lane == 0 ? (int)flag[ridx] : 0;
@@ -1271,7 +1301,10 @@ __global__ void __launch_bounds__(NT) k_mark_bm(const MarkJob *__restrict__ jobs
             int card = 0;
 #pragma unroll
             for (int w = 0; w < W; ++w) card += __popcll(x[w]);
-            if (card > maxcard) continue;  // no chunk set is large enough to hold it
+            if (card > maxcard) {  // no chunk set is large enough to hold it
+                if (J.r_perm) break;  // nor any later row of this warp (increasing cardinality)
+                continue;
+            }
             int limit = nb;
             if (ge) limit = (int)min((int64_t)nb, (int64_t)__ldg(ge + min(card, HN - 1)) - b0);
             if (limit <= 0) continue;

@@ -36,7 +36,7 @@ class sw_options(ctypes.Structure):
                 ("meet_b_tile", ctypes.c_int32), ("meet_f_rows", ctypes.c_int32),
                 ("meet_lane_words", ctypes.c_int32),
                 ("dir_theta", ctypes.c_double), ("set_cost", ctypes.c_double), ("reduce", ctypes.c_int32),
-                ("table_cap_slots", ctypes.c_int32)]
+                ("table_cap_slots", ctypes.c_int32), ("dir_rule", ctypes.c_int32)]
 
 
 def lib():
@@ -69,6 +69,8 @@ def lib():
         L.sw_last_stats.restype = i32
         L.sw_beam.argtypes = [i32, i32, p, p, p, sz, i64, i32, p, p, i32]
         L.sw_beam.restype = i32
+        L.sw_expmark.argtypes = [ctypes.c_double] * 4
+        L.sw_expmark.restype = ctypes.c_double
         L.sw_probe_int_peak.argtypes = [p, p, sz, p]
         L.sw_probe_int_peak.restype = i32
         L.sw_last_reduce_stats.argtypes = [p, p, p, p]
@@ -275,6 +277,11 @@ def sw_last_reduce_stats() -> dict:
     ms, pairs, steps, rows = ctypes.c_double(), ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int64()
     lib().sw_last_reduce_stats(ctypes.byref(ms), ctypes.byref(pairs), ctypes.byref(steps), ctypes.byref(rows))
     return {"mark_ms": ms.value, "mark_pairs": pairs.value, "mark_steps": steps.value, "mark_rows": rows.value}
+
+
+def sw_expmark(a_s: float, b_s: float, a_d: float, b_d: float) -> float:
+    """ExpMark of Section 2.1.2 (host computation in the library)."""
+    return float(lib().sw_expmark(a_s, b_s, a_d, b_d))
 
 
 def sw_probe_int_peak(stream=None) -> float:

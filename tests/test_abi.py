@@ -82,3 +82,17 @@ def test_options_roundtrip(lib):
     o.dir_theta = -3.0  # invalid: reset to the default
     sw.sw_set_options(o)
     assert sw.sw_get_options().dir_theta == 1.0
+
+
+def test_expmark_cost_estimate(lib):
+    # Section 2.1.2's ExpMark on the host (no GPU): a value worked out by
+    # hand (w = 1.5 / 0.95, exponent ln 1.5 / ln w = 0.8877, 1000^0.8877 =
+    # 460.4, factor 1.5 / 0.5 + 1 / (0.1 - 0.05) = 23), linear in Bs,
+    # increasing in As, and close to linear in As for very sparse A lists
+    v = sw.sw_expmark(1000, 1000, 0.1, 0.5)
+    assert abs(v / (1000 * 23 * 460.4) - 1) < 1e-3
+    assert abs(sw.sw_expmark(1000, 2000, 0.1, 0.5) / v - 2) < 1e-9
+    assert sw.sw_expmark(2000, 1000, 0.1, 0.5) > v
+    sparse = sw.sw_expmark(1e6, 10, 1e-6, 0.5) / sw.sw_expmark(1e5, 10, 1e-6, 0.5)
+    assert 9.9 < sparse < 10.0
+    assert sw.sw_expmark(0, 10, 0.1, 0.5) == 0.0

@@ -95,3 +95,13 @@ def test_cpu_baseline_line_counts_every_instance():
     assert "indices 0, 2, ... 6" in cpu["sample"] and "whole workload" in cpu["sample"]
     cpu = bench.cpu_baseline_line(ds, 4, 2, n_max=15)  # n = 12 .. 15: four instances
     assert "indices 0, 1, ... 3" in cpu["sample"] and "stratum n <= 15 (4 of 8" in cpu["sample"]
+
+
+def test_reference_arm_large_beam_is_unavailable():
+    line = _run_bench("--impl", "reference", "--workload", "beam5000")
+    assert line["impl"] == "reference" and "unavailable" in line
+
+
+def test_workloads_beam_shape():
+    ds, cfg = bench.workload("beam5000")
+    assert len(ds) == 1 and ds[0].shape == (2, 5000) and "beam n*ceil(log2 n) = 65000" in cfg["workload"]

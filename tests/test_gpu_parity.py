@@ -356,3 +356,30 @@ def test_table_overflow_fails_only_its_instance(sw, ws):
     r2, w2 = sw.sw_batch(hs, ws=ws)
     for i in (5, len(ds) - 1):
         assert (int(r2[i]), w2[i]) == oracle.bidir(ds[i])[:2]
+
+
+def test_expmark_direction_rule_same_results(sw, ws):
+    """The direction rule of ExpMark estimates (sw_options.dir_rule = 1,
+    Section 2.1.2) takes another schedule; r, the word and every level size
+    both schedules computed must be the same (they are properties of the
+    automaton), and oracle-exact."""
+    ds = gen.batch_random(32, 64, 128, 2, 4100)
+    hs = [sw.load(d) for d in ds]
+    r0, w0 = sw.sw_batch(hs, ws=ws)
+    s0 = [sw.sw_level_sizes(h) for h in hs]
+    old = sw.sw_get_options()
+    o = sw.sw_get_options()
+    o.dir_rule = 1
+    o.set_cost = 512.0
+    sw.sw_set_options(o)
+    try:
+        r1, w1 = sw.sw_batch(hs, ws=ws)
+        s1 = [sw.sw_level_sizes(h) for h in hs]
+    finally:
+        sw.sw_set_options(old)
+    assert (r0 == r1).all() and w0 == w1
+    for (f0, b0), (f1, b1) in zip(s0, s1):
+        m, mb = min(len(f0), len(f1)), min(len(b0), len(b1))
+        assert f0[:m] == f1[:m] and b0[:mb] == b1[:mb]
+    for i in (0, 5, 31):
+        assert (int(r1[i]), w1[i]) == oracle.bidir(ds[i])[:2]
