@@ -5,9 +5,10 @@ setting of the meet kernel's forward rows per tile and backward chunk size
 (lane words), of the direction rule (SetCost, the threshold theta of the
 step-cost comparison and its meet term, pair count or ExpMark, Section
 2.1.2), and of the inclusion reductions (none, or the BFS side's, Alg. 1),
-requires every candidate to return identical r (and identical words among
-candidates with the same reductions: a reduced BFS side returns another
-shortest word), and keeps the fastest.  Results are cached in tuned.json next to this file,
+requires every candidate to return identical r, and identical words among
+the candidates without reductions (with a reduced side the word depends on
+the depth at which the two searches met, so there each word must only
+reset the automaton and have length r), and keeps the fastest.  Results are cached in tuned.json next to this file,
 keyed by (words per set W, letters k, GPU name); `apply` loads the entry for
 a workload into the calling thread's options.
 
@@ -46,6 +47,13 @@ def _gpu_name() -> str:
     return torch.cuda.get_device_name(0)
 
 
+def _resets(delta: np.ndarray, word) -> bool:
+    states = np.arange(delta.shape[1])
+    for a in word:
+        states = delta[a][states]
+    return len(np.unique(states)) == 1
+
+
 def tune(automata, ws, grid=None, repeats: int = 2, verbose: bool = False) -> dict:
     """Times sw_batch over `automata` for every combination in `grid`
     (dict of option name -> values); returns {"best": {...}, "trials": [...]}."""
@@ -55,7 +63,7 @@ def tune(automata, ws, grid=None, repeats: int = 2, verbose: bool = False) -> di
     base = sw.sw_get_options()
     names = list(grid)
     ref_r = None
-    ref_words = {}  # per reduction setting
+    ref_words = None  # of the candidates without reductions
     trials = []
     try:
         for combo in itertools.product(*(grid[n] for n in names)):
@@ -75,10 +83,15 @@ def tune(automata, ws, grid=None, repeats: int = 2, verbose: bool = False) -> di
             red = int(getattr(o, "reduce", 0))
             if ref_r is None:
                 ref_r = r.copy()
-            if red not in ref_words:
-                ref_words[red] = w
-            if not ((r == ref_r).all() and w == ref_words[red]):
-                raise RuntimeError(f"setting {dict(zip(names, combo))} changed the results")
+            if not (r == ref_r).all():
+                raise RuntimeError(f"setting {dict(zip(names, combo))} changed r")
+            if red == 0:
+                if ref_words is None:
+                    ref_words = w
+                if w != ref_words:
+                    raise RuntimeError(f"setting {dict(zip(names, combo))} changed the words")
+            elif not all(len(wi) == ri and _resets(d, wi) for d, wi, ri in zip(automata, w, r)):
+                raise RuntimeError(f"setting {dict(zip(names, combo))} returned a word that does not reset")
             trial = dict(zip(names, combo))
             trial["seconds"] = best_t
             trials.append(trial)
