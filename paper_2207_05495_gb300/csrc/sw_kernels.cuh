@@ -919,7 +919,7 @@ __global__ void __launch_bounds__(NT) k_meet_bm(const MeetJob *__restrict__ jobs
     __shared__ unsigned long long s_best;
     constexpr int NW = NT / 32;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    unsigned long long my_pairs = 0, my_iters = 0, my_rows = 0;
+    unsigned long long my_rows = 0;
     for (;;) {
         if (threadIdx.x == 0) s_tile = (int64_t)atomicAdd(next_tile, 1ull);
         __syncthreads();
@@ -980,32 +980,51 @@ __global__ void __launch_bounds__(NT) k_meet_bm(const MeetJob *__restrict__ jobs
         //    f is the row's canonical position, and only the least meeting f
         //    matters, so rows at or past the best f found are passed over
         const int32_t *ge = J.ge_off >= 0 ? meta + J.ge_off : nullptr;
-        int64_t i = i0 + warp;
+        // row indices within the tile are 32-bit (a tile has at most
+        // tf_rows rows); the tile's rows start at permutation entry i0
+        const uint32_t *pt = perm + J.f_off + i0;
+        const uint4 *rt = rec + J.f_off;
+        const int ni = (int)(i1 - i0);
+        int li = warp;
         uint32_t f = 0, fn = 0;
         uint4 r = make_uint4(0, 0, 0, 0);
-        if (i < i1) {
-            f = __ldg(perm + J.f_off + i);
-            r = __ldg(rec + J.f_off + f);
+        if (li < ni) {
+            f = __ldg(pt + li);
+            r = __ldg(rt + f);
         }
-        if (i + NW < i1) fn = __ldg(perm + J.f_off + i + NW);
+        if (li + NW < ni) fn = __ldg(pt + li + NW);
         int last_card = -1, rows = 0;
+        // this warp's counts for the tile (rows tested since the last change
+        // of the bound, pairs, AND steps), added to the totals once per tile;
+        // 32 bits hold them: a warp tests at most 2^20 / 16 rows of a tile,
+        // each against at most 8192 sets and with at most 576 steps
+        uint32_t run_rows = 0, t_iters = 0, t_pairs = 0;
+        // the least meeting f known to this warp: rows at or past it are
+        // passed over.  It is re-read from the block's best every 8 rows and
+        // after each meet of this warp; a stale (larger) value only costs
+        // work, never a result, since every meet goes through atomicMin.
+        uint32_t best_f = 0xFFFFFFFFu;
         uint32_t mask[2 * LW];
         // this lane's units of a state bitmap start at sT + q * kStride + lbase
         const uint32_t *lbase = sT + lane * G::U;
-        for (; i < i1; i += NW) {
+        for (; li < ni; li += NW) {
             // prefetch: the record of the next row, the index of the one after
             uint32_t fnn = 0;
             uint4 rn = make_uint4(0, 0, 0, 0);
-            if (i + 2 * NW < i1) fnn = __ldg(perm + J.f_off + i + 2 * NW);
-            if (i + NW < i1) rn = __ldg(rec + J.f_off + fn);
-            // lane 0 reads the shared best; the whole warp follows its decision
+            if (li + 2 * NW < ni) fnn = __ldg(pt + li + 2 * NW);
+            if (li + NW < ni) rn = __ldg(rt + fn);
+            // lane 0 reads the shared best; the whole warp follows its value
             // (the walk's votes need every lane of the warp)
-            const int pass = __shfl_sync(
-                0xffffffffu, (int)((int64_t)(*(volatile unsigned long long *)&s_best >> 32) <= (int64_t)f), 0);
+            if (((li / NW) & 7) == 0)
+                best_f = __shfl_sync(0xffffffffu,
+                                     (uint32_t)(*(volatile unsigned long long *)&s_best >> 32), 0);
+            const bool pass = f >= best_f;
             // only the backward sets with at least |X| states can contain X;
             // rows come in increasing cardinality, so the bound changes rarely
             const int card = (int)(r.w >> 16);
             if (card != last_card) {
+                t_pairs += run_rows * (uint32_t)rows;
+                run_rows = 0;
                 int64_t end = ge ? (int64_t)__ldg(ge + min(card, HN - 1)) : J.b_cnt;
                 if (end <= b0) break;  // later rows have at least as many states: none fits here
                 rows = (int)min((int64_t)nb, end - b0);
@@ -1124,8 +1143,8 @@ __global__ void __launch_bounds__(NT) k_meet_bm(const MeetJob *__restrict__ jobs
                         }
                     }
                 }
-                my_iters += steps;
-                my_pairs += (unsigned long long)rows;
+                t_iters += steps;
+                ++run_rows;
                 if (alive) {  // every state of X processed: X lies inside the surviving sets
                     unsigned ball = __ballot_sync(0xffffffffu, la);
                     if (lane == __ffs(ball) - 1) {
@@ -1147,18 +1166,20 @@ __global__ void __launch_bounds__(NT) k_meet_bm(const MeetJob *__restrict__ jobs
                         atomicMin(&s_best, key);
                         atomicMin(best + J.slot, key);
                     }
+                    best_f = min(best_f, f);
                 }
             }
             f = fn;
             r = rn;
             fn = fnn;
         }
+        t_pairs += run_rows * (uint32_t)rows;
+        // per-warp counters: lanes counted the same rows and iterations
+        if (lane == 0 && t_iters) {
+            atomicAdd(pairs_done, (unsigned long long)t_pairs);
+            atomicAdd(and_iters, (unsigned long long)t_iters);
+        }
         __syncthreads();
-    }
-    // per-warp counters: lanes counted the same rows and iterations
-    if (lane == 0) {
-        if (my_pairs) atomicAdd(pairs_done, my_pairs);
-        if (my_iters) atomicAdd(and_iters, my_iters);
     }
     if (threadIdx.x == 0 && my_rows) atomicAdd(rows_transposed, my_rows);
 }
