@@ -581,7 +581,11 @@ def main():
                                "host_wall": sum(s["run_ms"] for s in stats) / len(stats),
                                "host_wait": sum(s["sync_ms"] for s in stats) / len(stats),
                                "host_select": sum(s["select_ms"] for s in stats) / len(stats),
-                               "host_update": sum(s["update_ms"] for s in stats) / len(stats)},
+                               "host_update": sum(s["update_ms"] for s in stats) / len(stats),
+                               **{k: sum(s[m] for s in stats) / len(stats)
+                                  for k, m in (("host_stage", "stage_ms"), ("host_plan", "plan_ms"),
+                                               ("host_post", "post_ms"), ("upload_fill_rehash", "table_ms"),
+                                               ("between_iterations", "gap_ms"))}},
         "iterations_per_step": st["iterations"], "waves": st["waves"], "evictions": st["evictions"],
         "arena_peak_sets": st["arena_peak"], "candidates_per_step": cand, "stored_sets_per_step": survivors,
         "one_at_a_time": {"value": m / one_s, "unit": "instances/s", "sample": f"first {m} instances",

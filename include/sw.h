@@ -261,6 +261,25 @@ int32_t sw_last_stats(int64_t *pairs, int64_t *candidates, int32_t *iterations,
                       int32_t *meet_lane_words);
 
 /*
+ * Where the calling thread's last search spent the time between kernels
+ * (no counterpart in the paper; the device figures need sw_set_timing(1)).
+ *   stage_ms:  host time building and uploading each iteration's jobs, from
+ *              the start of the iteration to its upload (the device waits);
+ *   plan_ms:   host time planning the next iteration while the meet kernel
+ *              runs (hidden behind it when the meet is longer);
+ *   post_ms:   host time after each meet's results arrive: recording meets,
+ *              recovering their words, retiring finished instances;
+ *   table_ms:  device time from each job upload to the expansion kernel
+ *              (the upload, the word recovery of the instances the previous
+ *              meet found, hash-table fills and rehashing);
+ *   gap_ms:    device time from the end of each meet kernel to the next
+ *              iteration's job upload (copies and idle time).
+ * Any pointer may be NULL.  Returns SW_OK.
+ */
+int32_t sw_last_host_stats(double *stage_ms, double *plan_ms, double *post_ms, double *table_ms,
+                           double *gap_ms);
+
+/*
  * Counters of the calling thread's last search with sw_options.reduce = 1
  * (the inclusion reductions of Alg. 1, Section 2.1).  mark_ms: device time
  * of the marking kernel (with timing on); mark_pairs: (set, set) pairs it

@@ -2,10 +2,13 @@
 
 It times the batched search on a sample of automata for every candidate
 setting of the meet kernel's forward rows per tile and backward chunk size
-(lane words), of the direction rule (SetCost, the threshold theta of the
+(lane words) and of the direction rule (SetCost, the threshold theta of the
 step-cost comparison and its meet term, pair count or ExpMark, Section
-2.1.2), and of the inclusion reductions (none, or the BFS side's, Alg. 1),
-requires every candidate to return identical r, and identical words among
+2.1.2); the inclusion reductions (Alg. 1) can be added to a grid.  A setting
+whose warm-up run on an eighth of the sample already takes longer than the
+best whole-sample time so far is dropped without timing, and tuning stops
+at a time limit with the best setting found.  It requires every candidate
+to return identical r, and identical words among
 the candidates without reductions (with a reduced side the word depends on
 the depth at which the two searches met, so there each word must only
 reset the automaton and have length r), and keeps the fastest.  Results are cached in tuned.json next to this file,
@@ -28,12 +31,15 @@ from . import gen, sw
 
 CACHE = os.path.join(os.path.dirname(os.path.abspath(__file__)), "tuned.json")
 
+# The reductions are left out of the default grid: on random automata of
+# 64..192 states they cost several times what they save (marking is
+# quadratic in the candidates), so they are only worth a grid of their own
+# for single hard instances.
 GRID = {
     "meet_f_rows": [4096, 16384],
     "meet_lane_words": [0, 4],
-    "set_cost": [512.0, 8192.0, 131072.0],
+    "set_cost": [128.0, 512.0, 8192.0, 131072.0],
     "dir_theta": [0.5, 1.0, 2.0],
-    "reduce": [0, 2],
     "dir_rule": [0, 1],
 }
 
@@ -54,9 +60,10 @@ def _resets(delta: np.ndarray, word) -> bool:
     return len(np.unique(states)) == 1
 
 
-def tune(automata, ws, grid=None, repeats: int = 2, verbose: bool = False) -> dict:
+def tune(automata, ws, grid=None, repeats: int = 2, verbose: bool = False, time_limit: float = 600.0) -> dict:
     """Times sw_batch over `automata` for every combination in `grid`
-    (dict of option name -> values); returns {"best": {...}, "trials": [...]}."""
+    (dict of option name -> values) until `time_limit` seconds have passed;
+    returns {"best": {...}, "trials": [...], "pruned": n, "complete": bool}."""
     import torch
     grid = grid or GRID
     hs = [sw.load(d) for d in automata]
@@ -65,13 +72,26 @@ def tune(automata, ws, grid=None, repeats: int = 2, verbose: bool = False) -> di
     ref_r = None
     ref_words = None  # of the candidates without reductions
     trials = []
+    pruned = 0
+    complete = True
+    t_start = time.perf_counter()
+    best_so_far = None
     try:
         for combo in itertools.product(*(grid[n] for n in names)):
+            if time.perf_counter() - t_start > time_limit:
+                complete = False
+                break
             o = sw.sw_get_options()
             for n, v in zip(names, combo):
                 setattr(o, n, v)
             sw.sw_set_options(o)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
             sw.sw_batch(hs[: max(1, len(hs) // 8)], ws=ws)  # warm
+            torch.cuda.synchronize()
+            if best_so_far is not None and time.perf_counter() - t0 > best_so_far:
+                pruned += 1
+                continue
             best_t = None
             for _ in range(repeats):
                 torch.cuda.synchronize()
@@ -95,12 +115,14 @@ def tune(automata, ws, grid=None, repeats: int = 2, verbose: bool = False) -> di
             trial = dict(zip(names, combo))
             trial["seconds"] = best_t
             trials.append(trial)
+            best_so_far = best_t if best_so_far is None else min(best_so_far, best_t)
             if verbose:
                 print(trial, flush=True)
     finally:
         sw.sw_set_options(base)
     best = min(trials, key=lambda t: t["seconds"])
-    return {"best": {n: best[n] for n in names}, "seconds": best["seconds"], "trials": trials}
+    return {"best": {n: best[n] for n in names}, "seconds": best["seconds"], "trials": trials, "pruned": pruned,
+            "complete": complete}
 
 
 def load_cache() -> dict:
@@ -139,9 +161,10 @@ def main():
     sample = gen.batch_random(512, 64, 192, 2, 0)
     W = max((d.shape[1] + 63) // 64 for d in sample)
     ws = sw.workspace(96 << 30)
-    res = tune(sample, ws, verbose=True)
+    res = tune(sample, ws, verbose=True, time_limit=300.0)
     save(key(W, 2, _gpu_name()), res)
-    print(json.dumps({"key": key(W, 2, _gpu_name()), "best": res["best"], "seconds": res["seconds"]}))
+    print(json.dumps({"key": key(W, 2, _gpu_name()), "best": res["best"], "seconds": res["seconds"],
+                      "trials": len(res["trials"]), "pruned": res["pruned"], "complete": res["complete"]}))
 
 
 if __name__ == "__main__":

@@ -53,6 +53,9 @@ struct Stats {
     int32_t waves = 0, evictions = 0;
     int64_t arena_peak = 0;  // most sets stored at once
     int32_t meet_lw = 0;     // bitmap meet: 64-bit words of the running AND per lane (0: direct test)
+    double stage_ms = 0, plan_ms = 0, post_ms = 0;  // host: job staging, planning during the meet, after the meet
+    double table_ms = 0;     // device: job upload, table fills and rehash before each expansion
+    double gap_ms = 0;       // device: from a meet's end to the next iteration's job upload
     double mark_ms = 0;      // inclusion reductions: device time of the marking kernel
     int64_t mark_pairs = 0, mark_steps = 0, mark_rows = 0;  // its pairs, AND steps, rows transposed
 };
@@ -139,7 +142,7 @@ struct Pinned {
         return p;
     }
 };
-thread_local Pinned g_up, g_down, g_words;
+thread_local Pinned g_up, g_down, g_words, g_wstat;
 
 // ---------------------------------------------------------------- pool allocator
 
@@ -198,7 +201,8 @@ struct Pool {
 
 // ---------------------------------------------------------------- per-instance state
 
-enum InstState { kWaiting = 0, kActive = 1, kDone = 2, kFailed = 3 };
+// kMet: a meet was found and the word is still being recovered
+enum InstState { kWaiting = 0, kActive = 1, kDone = 2, kFailed = 3, kMet = 4 };
 
 struct Level {
     int64_t off, cnt, cap;  // arena index, sets, slots reserved
@@ -658,7 +662,10 @@ OpTable ops_for(int W) {
 // ---------------------------------------------------------------- timing
 
 struct EventTimer {
-    cudaEvent_t ev[8] = {};
+    // 0..7: expansion, marking, compaction and meet bounds of an iteration;
+    // 8: its job upload; 9, 10: the end of the meet of alternate iterations
+    cudaEvent_t ev[11] = {};
+    int64_t meets = 0;  // meets recorded so far (selects ev[9] or ev[10])
     bool made = false;
     void ensure() {
         if (!made) {
@@ -805,6 +812,7 @@ struct Engine {
     }
 
     bool stage_begin() {
+        prestaged = false;
         stg.host = (char *)g_up.get(L.mirror_bytes);
         stg.dev = L.mirror;
         stg.cap = L.mirror_bytes;
@@ -1030,46 +1038,54 @@ struct Engine {
         }
     }
 
-    // One iteration over the active instances.  The next iteration's steps
-    // are planned on the host while this iteration's meet kernel runs.
-    int iterate() {
-        g_stats.iterations++;
-        auto t_sel = std::chrono::steady_clock::now();
-        // the allocation-free entry point (pageable staging) creates no CUDA
-        // objects: it waits for the whole stream instead of a counts event
-        const bool counts_event = !g_pageable;
-        if (counts_event && !ev_counts) CK(cudaEventCreateWithFlags(&ev_counts, cudaEventDisableTiming));
-        std::vector<Sel> sel;
-        sel.swap(pending);
-        plan(sel);  // instances without a planned step: new, or skipped for room
-        for (const Sel &s : sel) planned[s.id] = 0;
-        if (sel.empty()) {
-            // nothing fits: set back the instance holding the most memory
-            auto it = std::max_element(active.begin(), active.end(),
-                                       [&](int a, int b) { return I[a].footprint() < I[b].footprint(); });
-            int id = *it;
-            active.erase(it);
-            Inst &x = I[id];
-            g_stats.evictions++;
-            if (active.empty()) {  // it had all the room there is
-                finish(x, kFailed, SW_ENOMEM);
-            } else {
-                release(x);
-                x.state = kWaiting;
-                x.evictions++;
-                deferred.push_back(id);
-            }
-            return SW_OK;
-        }
+    // The job arrays of one iteration in the staging buffer (host side, for
+    // patching before the upload, and the device addresses they go to).
+    struct Staged {
+        int nj = 0, n_mark = 0, nfill = 0, nsegs = 0, tf_rows = 0;
+        int64_t ncand = 0, rehash_total = 0, maxfill = 1;
+        bool marking = false;
+        ExpandJob *jobs = nullptr, *d_jobs = nullptr;
+        MeetJob *mj = nullptr, *d_mj = nullptr;
+        FillJob *d_fill = nullptr;
+        RehashSeg *d_segs = nullptr;
+        MarkJob *d_mark = nullptr;
+        int64_t *d_mark_nt = nullptr;
+    };
+    // Word jobs staged with an iteration's jobs; their results are read
+    // back with that iteration's level sizes.
+    struct WordBatch {
+        std::vector<WordJob> wj;
+        WordJob *d_wj = nullptr;
+        int64_t *d_bl = nullptr;
+        int64_t area = 0;
+        uint32_t *status = nullptr;  // host copy of the word statuses
+        uint8_t *hwd = nullptr;      // host copy of the word area (host words)
+    };
+    // The steps planned while the last meet ran are staged at once (plain
+    // searches); prestaged says that the staging buffer holds them.  Any
+    // other use of the staging buffer clears it.
+    Staged pre;
+    bool prestaged = false;
+    // Instances whose meet was found (state kMet) and whose words are still
+    // to be recovered, with their best (f, b) keys.
+    std::vector<int> met_ids;
+    std::vector<unsigned long long> met_best;
+
+    // Builds the job arrays of `sel` in the staging buffer (without the
+    // upload).  A step of an instance that is no longer active gets empty
+    // jobs: no candidates and no meet tiles.
+    int build_stage(std::vector<Sel> &sel, Staged &S) {
+        S = Staged{};
         if (!stage_begin()) return SW_ECUDA;
         // jobs, table fills and rehash segments: one upload
-        int nj = (int)sel.size();
-        ExpandJob *d_jobs = nullptr;
-        ExpandJob *jobs = stg.take<ExpandJob>(nj, &d_jobs);
+        const int nj = (int)sel.size();
+        S.nj = nj;
+        S.jobs = stg.take<ExpandJob>(nj, &S.d_jobs);
         if (!stg.ok) return SW_EINTERNAL;
+        ExpandJob *jobs = S.jobs;
         std::vector<FillJob> fills;
         std::vector<RehashSeg> segs;
-        int64_t cand = 0, rehash_total = 0, maxfill = 1;
+        int64_t cand = 0;
         for (int t = 0; t < nj; ++t) {
             Sel &s = sel[t];
             Inst &x = I[s.id];
@@ -1077,7 +1093,7 @@ struct Engine {
             ExpandJob &J = jobs[t];
             J.cand_off = cand;
             J.parent_off = P.off;
-            J.parent_cnt = P.cnt;
+            J.parent_cnt = x.state == kActive ? P.cnt : 0;
             J.delta_off = x.delta_off;
             J.dest_off = s.dest;
             J.tab_off = rdir[s.d] ? s.new_tab : x.tab_off[s.d];
@@ -1090,22 +1106,22 @@ struct Engine {
             cand += round_up(s.nc, kScanBlock);
             if (rdir[s.d]) {
                 fills.push_back({s.new_tab, s.new_cap});
-                maxfill = std::max(maxfill, s.new_cap);
+                S.maxfill = std::max(S.maxfill, s.new_cap);
             } else if (s.new_tab >= 0) {
                 fills.push_back({s.new_tab, s.new_cap});
-                maxfill = std::max(maxfill, s.new_cap);
+                S.maxfill = std::max(S.maxfill, s.new_cap);
                 for (auto &l : x.lev[s.d]) {
-                    segs.push_back({rehash_total, l.off, l.cnt, s.new_tab, s.new_cap, s.d, s.id});
-                    rehash_total += l.cnt;
+                    segs.push_back({S.rehash_total, l.off, l.cnt, s.new_tab, s.new_cap, s.d, s.id});
+                    S.rehash_total += l.cnt;
                 }
             }
         }
-        const int64_t ncand = cand;
-        FillJob *d_fill = nullptr;
-        RehashSeg *d_segs = nullptr;
+        S.ncand = cand;
+        S.nfill = (int)fills.size();
+        S.nsegs = (int)segs.size();
         if (!fills.empty()) {
-            FillJob *f = stg.take<FillJob>(fills.size(), &d_fill);
-            RehashSeg *g = stg.take<RehashSeg>(std::max<size_t>(segs.size(), 1), &d_segs);
+            FillJob *f = stg.take<FillJob>(fills.size(), &S.d_fill);
+            RehashSeg *g = stg.take<RehashSeg>(std::max<size_t>(segs.size(), 1), &S.d_segs);
             if (!stg.ok) return SW_EINTERNAL;
             std::memcpy(f, fills.data(), fills.size() * sizeof(FillJob));
             if (!segs.empty()) std::memcpy(g, segs.data(), segs.size() * sizeof(RehashSeg));
@@ -1113,27 +1129,23 @@ struct Engine {
         // inclusion reductions: per job a self-reduction job over its own
         // candidates and one job per kept level of its direction (the
         // history); the tiles of all of them are numbered in one range
-        MarkJob *d_mark = nullptr;
-        int64_t *d_mark_nt = nullptr;
-        int n_mark = 0;
         // the two-phase flags (winners, marks, survivors) are needed when
         // any job of this iteration expands a reduced side; the other jobs
         // get no marks, so phase 2 counts exactly their winners
-        bool marking = false;
-        for (const Sel &sl : sel) marking |= rdir[sl.d];
-        if (marking) {
+        for (const Sel &sl : sel) S.marking |= rdir[sl.d];
+        if (S.marking) {
             size_t cnt = 0;
             for (const Sel &sl : sel)
                 if (rdir[sl.d]) cnt += I[sl.id].lev[sl.d].size() + 1;
-            MarkJob *mk = stg.take<MarkJob>(std::max<size_t>(cnt, 1), &d_mark);
-            int64_t *nt = stg.take<int64_t>(2, &d_mark_nt);
+            MarkJob *mk = stg.take<MarkJob>(std::max<size_t>(cnt, 1), &S.d_mark);
+            int64_t *nt = stg.take<int64_t>(2, &S.d_mark_nt);
             if (!stg.ok) return SW_EINTERNAL;
             const int64_t kr = (int64_t)2048 * (mc.lw == 4 ? bm_lanes_words(W) : mc.lw);  // chunk rows
             int64_t tiles = 0;
             auto add = [&](int64_t r_off, int64_t r_cnt, int r_cand, int64_t c_off, int64_t c_cnt, int c_cand,
                            int64_t ge, int col, int self, int r_perm) {
                 if (r_cnt <= 0 || c_cnt <= 0) return;
-                MarkJob &M = mk[n_mark++];
+                MarkJob &M = mk[S.n_mark++];
                 M.tile_off = tiles;
                 M.ntc = (c_cnt + kr - 1) / kr;
                 M.r_off = r_off;
@@ -1151,7 +1163,7 @@ struct Engine {
             };
             for (int t = 0; t < nj; ++t) {
                 const Sel &sl = sel[t];
-                if (!rdir[sl.d]) continue;
+                if (!rdir[sl.d] || jobs[t].parent_cnt == 0) continue;
                 const Inst &x = I[sl.id];
                 const int64_t co = jobs[t].cand_off, cn = sl.nc;
                 if (sl.d == 0) {
@@ -1168,14 +1180,13 @@ struct Engine {
         }
         // meet jobs: the size of the level each job produces is filled in on
         // the device (k_meet_prep), so the meet follows without a host sync
-        MeetJob *d_mj = nullptr;
-        MeetJob *mj = stg.take<MeetJob>(nj, &d_mj);
+        S.mj = stg.take<MeetJob>(nj, &S.d_mj);
         if (!stg.ok) return SW_EINTERNAL;
         // A launch with few tiles gets shorter forward tiles (down to 1024
         // rows): more transposes, fewer idle SMs at its end.  The sizes of
         // the new levels are predicted from their last duplicate ratios.
-        int tf_rows = mc.tf_rows;
-        if (mc.algo == 0 && tf_rows > 1024) {
+        S.tf_rows = mc.tf_rows;
+        if (mc.algo == 0 && S.tf_rows > 1024) {
             std::vector<std::pair<double, double>> fb((size_t)nj);
             for (int t = 0; t < nj; ++t) {
                 const Sel &s = sel[t];
@@ -1190,12 +1201,12 @@ struct Engine {
                 return n;
             };
             const double want = 8.0 * sm_count();
-            while (tf_rows > 1024 && tiles_for(tf_rows) < want) tf_rows /= 2;
+            while (S.tf_rows > 1024 && tiles_for(S.tf_rows) < want) S.tf_rows /= 2;
         }
         for (int t = 0; t < nj; ++t) {
             Sel &s = sel[t];
             Inst &x = I[s.id];
-            MeetJob &M = mj[t];
+            MeetJob &M = S.mj[t];
             M.f_off = s.d == 0 ? s.dest : x.lev[0].back().off;
             M.f_cnt = s.d == 0 ? 0 : x.lev[0].back().cnt;
             M.b_off = s.d == 1 ? s.dest : x.lev[1].back().off;
@@ -1206,23 +1217,233 @@ struct Engine {
             M.ge_off = s.d == 1 ? s.ge : x.lev[1].back().ge;
             M.upd = s.d;
             M.count_idx = t;
+            if (jobs[t].parent_cnt == 0) empty_meet(M);
         }
+        return SW_OK;
+    }
+
+    // A meet job with no tiles (its instance met or failed after the step was planned).
+    static void empty_meet(MeetJob &M) {
+        M.f_cnt = 0;
+        M.b_cnt = 0;
+        M.upd = -1;
+    }
+
+    // Stages word jobs for met[pos ..] (as many as the staging buffer holds;
+    // when force_first, at least one) and advances pos.  An instance whose
+    // word does not fit in its output ends here with its error.
+    int stage_words(const std::vector<int> &met, const std::vector<unsigned long long> &best, size_t &pos,
+                    WordBatch &wb, bool force_first) {
+        std::vector<int64_t> blev;
+        for (; pos < met.size(); ++pos) {
+            Inst &x = I[met[pos]];
+            int i = (int)x.lev[0].size() - 1, j = (int)x.lev[1].size() - 1;
+            int r = i + j;
+            x.r = r;
+            if (r > x.word_cap) {
+                finish(x, kFailed, SW_EWORDCAP);
+                continue;
+            }
+            if (!device_words && r > L.word_area_cap) {
+                finish(x, kFailed, SW_ENOMEM);
+                continue;
+            }
+            size_t need = (wb.wj.size() + 1) * sizeof(WordJob) + (blev.size() + 3 * j) * sizeof(int64_t) + 1024;
+            const bool room = stg.fits(need) && (device_words || wb.area + r <= L.word_area_cap);
+            if (!room && !(force_first && wb.wj.empty())) break;
+            WordJob J;
+            J.f_arena = x.lev[0].back().off + (int64_t)(best[pos] >> 32);
+            J.blev = (int64_t)(blev.size() / 3);
+            J.word_off = device_words ? x.word_off : wb.area;
+            J.delta_off = x.delta_off;
+            J.i = i;
+            J.j = j;
+            J.n = x.n;
+            J.k = x.k;
+            J.slot = (int32_t)wb.wj.size();
+            J.pad = met[pos];
+            for (int m = 0; m < j; ++m) {
+                blev.push_back(x.lev[1][m].off);
+                blev.push_back(x.lev[1][m].cnt);
+                blev.push_back(x.lev[1][m].ge);
+            }
+            if (!device_words) wb.area += r;
+            wb.wj.push_back(J);
+        }
+        if (wb.wj.empty()) return SW_OK;
+        const int nw = (int)wb.wj.size();
+        WordJob *hw = stg.take<WordJob>(nw, &wb.d_wj);
+        int64_t *hb = stg.take<int64_t>(std::max<size_t>(blev.size(), 3), &wb.d_bl);
+        if (!stg.ok) return SW_EINTERNAL;
+        std::memcpy(hw, wb.wj.data(), nw * sizeof(WordJob));
+        if (!blev.empty()) std::memcpy(hb, blev.data(), blev.size() * sizeof(int64_t));
+        return SW_OK;
+    }
+
+    // Queues the word kernel of a staged (and uploaded) batch and the copies
+    // of its results.
+    int launch_words(WordBatch &wb) {
+        const int nw = (int)wb.wj.size();
+        uint8_t *base = device_words ? out_words : L.word_area;
+        if (g_timing) CK(cudaEventRecord(g_ev.ev[5], st));
+        CK(ops.words(wb.d_wj, wb.d_bl, nw, base, L, st));
+        if (g_timing) CK(cudaEventRecord(g_ev.ev[6], st));
+        wb.status = (uint32_t *)g_wstat.get(nw * sizeof(uint32_t));
+        if (!wb.status) return SW_ECUDA;
+        CK(cudaMemcpyAsync(wb.status, L.word_status, nw * sizeof(uint32_t), cudaMemcpyDeviceToHost, st));
+        wb.hwd = nullptr;
+        if (!device_words && wb.area > 0) {
+            wb.hwd = (uint8_t *)g_words.get((size_t)wb.area);
+            if (!wb.hwd) return SW_ECUDA;
+            CK(cudaMemcpyAsync(wb.hwd, L.word_area, (size_t)wb.area, cudaMemcpyDeviceToHost, st));
+        }
+        return SW_OK;
+    }
+
+    // Once the stream has passed a batch's copies: every instance of it ends.
+    void collect_words(WordBatch &wb) {
+        if (g_timing) g_stats.words_ms += elapsed(g_ev.ev[5], g_ev.ev[6]);
+        for (size_t t = 0; t < wb.wj.size(); ++t) {
+            Inst &x = I[wb.wj[t].pad];
+            if (wb.status[t] != 0) {
+                finish(x, kFailed, SW_EINTERNAL);
+                continue;
+            }
+            if (!device_words && out_words)
+                std::memcpy(out_words + x.word_off, wb.hwd + wb.wj[t].word_off, (size_t)x.r);
+            finish(x, kDone, SW_OK);
+        }
+        wb.wj.clear();
+    }
+
+    // Recovers the words of met instances now (batch by batch, waiting for each).
+    int recover_words(const std::vector<int> &met, const std::vector<unsigned long long> &best) {
+        size_t pos = 0;
+        while (pos < met.size()) {
+            if (!stage_begin()) return SW_ECUDA;
+            WordBatch wb;
+            int rc = stage_words(met, best, pos, wb, true);
+            if (rc) return rc;
+            if (wb.wj.empty()) continue;
+            rc = stage_flush();
+            if (rc) return rc;
+            rc = launch_words(wb);
+            if (rc) return rc;
+            CK(wait_stream(st));
+            collect_words(wb);
+        }
+        return SW_OK;
+    }
+
+    // One iteration over the active instances.  The next iteration's steps
+    // are planned, and for a plain search staged, on the host while this
+    // iteration's meet kernel runs.  The words of the instances that meet
+    // finds are recovered at the start of the next iteration, ahead of its
+    // expansion (so the device goes from one meet to the next expansion
+    // without waiting for the host), and end with that iteration's level
+    // sizes; a step staged for an instance that met is emptied.
+    int iterate() {
+        g_stats.iterations++;
+        auto t_sel = std::chrono::steady_clock::now();
+        // the allocation-free entry point (pageable staging) creates no CUDA
+        // objects: it waits for the whole stream instead of a counts event
+        const bool counts_event = !g_pageable;
+        if (counts_event && !ev_counts) CK(cudaEventCreateWithFlags(&ev_counts, cudaEventDisableTiming));
+        std::vector<Sel> sel;
+        sel.swap(pending);
+        // the staged jobs serve when every active instance has its step in them
+        bool use_pre = prestaged;
+        if (use_pre)
+            for (int id : active)
+                if (!planned[id]) use_pre = false;
+        if (!use_pre) {
+            // steps planned for instances that have since met or failed go,
+            // with their memory (kept by the instance until it ends)
+            sel.erase(std::remove_if(sel.begin(), sel.end(),
+                                     [&](const Sel &s) {
+                                         if (I[s.id].state == kActive) return false;
+                                         planned[s.id] = 0;
+                                         if (rdir[s.d]) tab_pool.release(s.new_tab, s.new_cap);
+                                         return true;
+                                     }),
+                      sel.end());
+            plan(sel);  // instances without a planned step: new, or skipped for room
+        }
+        for (const Sel &s : sel) planned[s.id] = 0;
+        if (sel.empty()) {
+            prestaged = false;
+            int rc = met_ids.empty() ? SW_OK : recover_words(met_ids, met_best);
+            met_ids.clear();
+            met_best.clear();
+            if (rc) return rc;
+            if (active.empty()) return SW_OK;
+            // nothing fits: set back the instance holding the most memory
+            auto it = std::max_element(active.begin(), active.end(),
+                                       [&](int a, int b) { return I[a].footprint() < I[b].footprint(); });
+            int id = *it;
+            active.erase(it);
+            Inst &x = I[id];
+            g_stats.evictions++;
+            if (active.empty()) {  // it had all the room there is
+                finish(x, kFailed, SW_ENOMEM);
+            } else {
+                release(x);
+                x.state = kWaiting;
+                x.evictions++;
+                deferred.push_back(id);
+            }
+            return SW_OK;
+        }
+        Staged S;
+        if (use_pre) {
+            S = pre;
+            for (int t = 0; t < S.nj; ++t)
+                if (I[sel[t].id].state != kActive) {
+                    S.jobs[t].parent_cnt = 0;
+                    empty_meet(S.mj[t]);
+                }
+        } else {
+            int rc = build_stage(sel, S);
+            if (rc) return rc;
+        }
+        prestaged = false;
+        const int nj = S.nj;
+        const int64_t ncand = S.ncand;
+        const bool marking = S.marking;
+        // the words of the instances the last meet found, in the same upload
+        WordBatch wb;
+        if (!met_ids.empty()) {
+            size_t pos = 0;
+            int rc = stage_words(met_ids, met_best, pos, wb, false);
+            if (rc) return rc;
+            met_ids.erase(met_ids.begin(), met_ids.begin() + (std::ptrdiff_t)pos);
+            met_best.erase(met_best.begin(), met_best.begin() + (std::ptrdiff_t)pos);
+        }
+        if (g_timing) CK(cudaEventRecord(g_ev.ev[8], st));
         int rc = stage_flush();
         if (rc) return rc;
-        g_stats.select_ms +=
-            std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t_sel).count();
+        if (!wb.wj.empty()) {
+            rc = launch_words(wb);
+            if (rc) return rc;
+        }
+        {
+            const double ms =
+                std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t_sel).count();
+            g_stats.select_ms += ms;
+            g_stats.stage_ms += ms;
+        }
         g_stats.candidates += ncand;
-        if (!fills.empty()) CK(ops.fill(d_fill, (int)fills.size(), maxfill, L, st));
-        if (!segs.empty()) CK(ops.rehash(d_segs, (int)segs.size(), rehash_total, L, st));
+        if (S.nfill) CK(ops.fill(S.d_fill, S.nfill, S.maxfill, L, st));
+        if (S.nsegs) CK(ops.rehash(S.d_segs, S.nsegs, S.rehash_total, L, st));
         if (marking) CK(cudaMemsetAsync(L.pairs + 3, 0, 3 * sizeof(unsigned long long), st));
         if (g_timing) CK(cudaEventRecord(g_ev.ev[0], st));
-        CK(ops.expand(d_jobs, nj, ncand, L, st));
+        CK(ops.expand(S.d_jobs, nj, ncand, L, st));
         if (g_timing) CK(cudaEventRecord(g_ev.ev[1], st));
         if (marking) {
-            CK(ops.mark(d_jobs, nj, ncand, d_mark, n_mark, d_mark_nt, mc, L, st));
+            CK(ops.mark(S.d_jobs, nj, ncand, S.d_mark, S.n_mark, S.d_mark_nt, mc, L, st));
             if (g_timing) CK(cudaEventRecord(g_ev.ev[7], st));
         }
-        CK(ops.compact(d_jobs, nj, ncand, marking ? 2 : 0, L, st));
+        CK(ops.compact(S.d_jobs, nj, ncand, marking ? 2 : 0, L, st));
         if (g_timing) CK(cudaEventRecord(g_ev.ev[2], st));
         // the new levels' sizes and the status come back before the meet
         uint64_t *down = (uint64_t *)g_down.get((3 * nj + 8) * sizeof(uint64_t));
@@ -1240,8 +1461,11 @@ struct Engine {
                                        cudaMemcpyDeviceToHost, st));
         CK(cudaMemsetAsync(L.pairs, 0, 3 * sizeof(unsigned long long), st));
         if (g_timing) CK(cudaEventRecord(g_ev.ev[3], st));
-        CK(ops.meet(d_mj, nj, mc, tf_rows, L, st));
-        if (g_timing) CK(cudaEventRecord(g_ev.ev[4], st));
+        CK(ops.meet(S.d_mj, nj, mc, S.tf_rows, L, st));
+        if (g_timing) {
+            CK(cudaEventRecord(g_ev.ev[4], st));
+            CK(cudaEventRecord(g_ev.ev[9 + (g_ev.meets & 1)], st));
+        }
         g_stats.meet_launches++;
         CK(cudaMemcpyAsync(d_best, L.best, nj * sizeof(unsigned long long), cudaMemcpyDeviceToHost, st));
         CK(cudaMemcpyAsync(d_pairs, L.pairs, 3 * sizeof(unsigned long long), cudaMemcpyDeviceToHost, st));
@@ -1254,6 +1478,8 @@ struct Engine {
         } else {
             CK(wait_stream(st));
         }
+        // the words queued ahead of this iteration are back: their instances end
+        if (!wb.wj.empty()) collect_words(wb);
         if ((uint32_t)(*d_status & 0xFFFFFFFFu) & kStatusTableFull) {
             // a hash table could not take every set of an instance (its
             // probes ran out): that instance fails with SW_ENOMEM, the others
@@ -1276,7 +1502,7 @@ struct Engine {
         for (int t = 0; t < nj; ++t) {
             Sel &s = sel[t];
             Inst &x = I[s.id];
-            if (x.state != kActive) continue;  // failed above: its memory is already released
+            if (x.state != kActive) continue;  // met earlier, or failed above: its step was empty or is void
             int64_t c = (int64_t)down[t];
             inst_shrink(x, s.dest, s.nc, c);
             x.lev[s.d].push_back({s.dest, c, c, s.ge});
@@ -1287,14 +1513,30 @@ struct Engine {
         }
         g_stats.update_ms +=
             std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t_upd).count();
-        // plan the next iteration while the meet kernel runs; a step planned
-        // for an instance that meets now is dropped below with its memory
+        // plan (and for a plain search stage) the next iteration while the
+        // meet kernel runs; a step planned for an instance that meets now is
+        // emptied or dropped next time
         auto t_plan = std::chrono::steady_clock::now();
         plan(pending);
-        g_stats.select_ms +=
-            std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t_plan).count();
+        if (!pending.empty() && !rdir[0] && !rdir[1]) {
+            rc = build_stage(pending, pre);
+            if (rc) return rc;
+            prestaged = true;
+        }
+        {
+            const double ms =
+                std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t_plan).count();
+            g_stats.select_ms += ms;
+            g_stats.plan_ms += ms;
+        }
         CK(wait_stream(st));
+        const auto t_post = std::chrono::steady_clock::now();
         if (g_timing) {
+            // device time from the previous meet's end to this upload, and
+            // from the upload to the expansion (fills, rehash)
+            if (g_ev.meets > 0) g_stats.gap_ms += elapsed(g_ev.ev[9 + ((g_ev.meets - 1) & 1)], g_ev.ev[8]);
+            g_ev.meets++;
+            g_stats.table_ms += elapsed(g_ev.ev[8], g_ev.ev[0]);
             g_stats.expand_ms += elapsed(g_ev.ev[0], g_ev.ev[1]);
             if (marking) {
                 g_stats.mark_ms += elapsed(g_ev.ev[1], g_ev.ev[7]);
@@ -1315,110 +1557,32 @@ struct Engine {
         g_stats.pairs += (int64_t)d_pairs[0];
         g_stats.and_iters += (int64_t)d_pairs[1];
         g_stats.rows_transposed += (int64_t)d_pairs[2];
-        std::vector<int> met;
-        std::vector<unsigned long long> best;
         for (int t = 0; t < nj; ++t) {
-            if (I[sel[t].id].state != kActive || d_best[t] == ~0ull) continue;
-            met.push_back(sel[t].id);
-            best.push_back(d_best[t]);
+            Inst &x = I[sel[t].id];
+            if (x.state != kActive || d_best[t] == ~0ull) continue;
+            x.state = kMet;
+            met_ids.push_back(sel[t].id);
+            met_best.push_back(d_best[t]);
         }
-        if (!met.empty()) {
-            rc = recover_words(met, best);
-            if (rc) return rc;
-        }
-        // finished instances took their memory, planned steps included, with them
-        pending.erase(std::remove_if(pending.begin(), pending.end(),
-                                     [&](const Sel &s) {
-                                         if (I[s.id].state == kActive) return false;
-                                         planned[s.id] = 0;
-                                         if (rdir[s.d]) tab_pool.release(s.new_tab, s.new_cap);
-                                         return true;
-                                     }),
-                      pending.end());
         active.erase(std::remove_if(active.begin(), active.end(), [&](int id) { return I[id].state != kActive; }),
                      active.end());
-        g_stats.arena_peak = std::max(g_stats.arena_peak, set_pool.used);
-        return SW_OK;
-    }
-
-    int recover_words(const std::vector<int> &met, const std::vector<unsigned long long> &best) {
-        size_t pos = 0;
-        while (pos < met.size()) {
-            if (!stage_begin()) return SW_ECUDA;
-            std::vector<WordJob> wj;
-            std::vector<int64_t> blev;
-            int64_t area = 0;
-            for (; pos < met.size(); ++pos) {
-                Inst &x = I[met[pos]];
-                int i = (int)x.lev[0].size() - 1, j = (int)x.lev[1].size() - 1;
-                int r = i + j;
-                x.r = r;
-                if (r > x.word_cap) {
-                    finish(x, kFailed, SW_EWORDCAP);
-                    continue;
-                }
-                if (!device_words && r > L.word_area_cap) {
-                    finish(x, kFailed, SW_ENOMEM);
-                    continue;
-                }
-                size_t need = (wj.size() + 1) * sizeof(WordJob) + (blev.size() + 3 * j) * sizeof(int64_t) + 1024;
-                if (!wj.empty() && (!stg.fits(need) || (!device_words && area + r > L.word_area_cap))) break;
-                WordJob J;
-                J.f_arena = x.lev[0].back().off + (int64_t)(best[pos] >> 32);
-                J.blev = (int64_t)(blev.size() / 3);
-                J.word_off = device_words ? x.word_off : area;
-                J.delta_off = x.delta_off;
-                J.i = i;
-                J.j = j;
-                J.n = x.n;
-                J.k = x.k;
-                J.slot = (int32_t)wj.size();
-                J.pad = met[pos];
-                for (int m = 0; m < j; ++m) {
-                    blev.push_back(x.lev[1][m].off);
-                    blev.push_back(x.lev[1][m].cnt);
-                    blev.push_back(x.lev[1][m].ge);
-                }
-                if (!device_words) area += r;
-                wj.push_back(J);
-            }
-            if (wj.empty()) continue;
-            int nw = (int)wj.size();
-            WordJob *d_wj = nullptr;
-            int64_t *d_bl = nullptr;
-            WordJob *hw = stg.take<WordJob>(nw, &d_wj);
-            int64_t *hb = stg.take<int64_t>(std::max<size_t>(blev.size(), 3), &d_bl);
-            if (!stg.ok) return SW_EINTERNAL;
-            std::memcpy(hw, wj.data(), nw * sizeof(WordJob));
-            if (!blev.empty()) std::memcpy(hb, blev.data(), blev.size() * sizeof(int64_t));
-            int rc = stage_flush();
+        if (active.empty()) {
+            // no iteration follows to carry the words: recover them now
+            prestaged = false;
+            rc = met_ids.empty() ? SW_OK : recover_words(met_ids, met_best);
+            met_ids.clear();
+            met_best.clear();
             if (rc) return rc;
-            uint8_t *base = device_words ? out_words : L.word_area;
-            if (g_timing) CK(cudaEventRecord(g_ev.ev[5], st));
-            CK(ops.words(d_wj, d_bl, nw, base, L, st));
-            if (g_timing) CK(cudaEventRecord(g_ev.ev[6], st));
-            uint32_t *ws = (uint32_t *)g_down.get(nw * sizeof(uint32_t));
-            if (!ws) return SW_ECUDA;
-            CK(cudaMemcpyAsync(ws, L.word_status, nw * sizeof(uint32_t), cudaMemcpyDeviceToHost, st));
-            uint8_t *hwd = nullptr;
-            if (!device_words && area > 0) {
-                hwd = (uint8_t *)g_words.get((size_t)area);
-                if (!hwd) return SW_ECUDA;
-                CK(cudaMemcpyAsync(hwd, L.word_area, (size_t)area, cudaMemcpyDeviceToHost, st));
+            // finished instances took their memory, planned steps included, with them
+            for (const Sel &s : pending) {
+                planned[s.id] = 0;
+                if (rdir[s.d]) tab_pool.release(s.new_tab, s.new_cap);
             }
-            CK(wait_stream(st));
-            if (g_timing) g_stats.words_ms += elapsed(g_ev.ev[5], g_ev.ev[6]);
-            for (int t = 0; t < nw; ++t) {
-                Inst &x = I[wj[t].pad];
-                if (ws[t] != 0) {
-                    finish(x, kFailed, SW_EINTERNAL);
-                    continue;
-                }
-                if (!device_words && out_words)
-                    std::memcpy(out_words + x.word_off, hwd + wj[t].word_off, (size_t)x.r);
-                finish(x, kDone, SW_OK);
-            }
+            pending.clear();
         }
+        g_stats.arena_peak = std::max(g_stats.arena_peak, set_pool.used);
+        g_stats.post_ms +=
+            std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t_post).count();
         return SW_OK;
     }
 
@@ -1764,7 +1928,10 @@ static int32_t run_instances(std::vector<Inst> &I, const std::vector<uint16_t> *
                              const int32_t *d_delta32, const std::vector<int64_t> *src_off, cudaStream_t st,
                              void *ws, size_t ws_bytes, bool device_words, uint8_t *out_words) {
     g_stats = Stats{};
-    if (g_timing) g_ev.ensure();
+    if (g_timing) {
+        g_ev.ensure();
+        g_ev.meets = 0;
+    }
     int W = common_w(I);
     int64_t delta_elems = 0;
     for (auto &x : I) delta_elems = std::max(delta_elems, x.delta_off + (int64_t)x.n * x.k);
@@ -1992,6 +2159,15 @@ void sw_set_options(const sw_options *opt) {
 }
 
 double sw_expmark(double a_s, double b_s, double a_d, double b_d) { return expmark(a_s, b_s, a_d, b_d); }
+
+int32_t sw_last_host_stats(double *stage_ms, double *plan_ms, double *post_ms, double *table_ms, double *gap_ms) {
+    if (stage_ms) *stage_ms = g_stats.stage_ms;
+    if (plan_ms) *plan_ms = g_stats.plan_ms;
+    if (post_ms) *post_ms = g_stats.post_ms;
+    if (table_ms) *table_ms = g_stats.table_ms;
+    if (gap_ms) *gap_ms = g_stats.gap_ms;
+    return SW_OK;
+}
 
 int32_t sw_last_reduce_stats(double *mark_ms, int64_t *mark_pairs, int64_t *mark_steps, int64_t *mark_rows) {
     if (mark_rows) *mark_rows = g_stats.mark_rows;

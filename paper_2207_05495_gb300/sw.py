@@ -75,6 +75,8 @@ def lib():
         L.sw_probe_int_peak.restype = i32
         L.sw_last_reduce_stats.argtypes = [p, p, p, p]
         L.sw_last_reduce_stats.restype = i32
+        L.sw_last_host_stats.argtypes = [p] * 5
+        L.sw_last_host_stats.restype = i32
         L.sw_set_timing.argtypes = [i32]
         L.sw_set_timing.restype = None
         L.sw_get_options.argtypes = [p]
@@ -246,9 +248,11 @@ def sw_batch_device(n, k, d_delta, delta_off, stream=None, ws=None, d_r=None, d_
 
 def sw_last_stats() -> dict:
     """Counters of the calling thread's last search (sw_last_stats), with
-    the marking kernel's (sw_last_reduce_stats) under the keys mark_*."""
+    the marking kernel's (sw_last_reduce_stats) under the keys mark_* and
+    the time between kernels (sw_last_host_stats)."""
     d = _last_stats()
     d.update(sw_last_reduce_stats())
+    d.update(sw_last_host_stats())
     return d
 
 
@@ -271,6 +275,12 @@ def _last_stats() -> dict:
             "and_iters": iters.value, "rows_transposed": rows.value, "words_ms": wms.value,
             "run_ms": rms.value, "sync_ms": sms.value, "select_ms": sel.value, "update_ms": upd.value,
             "meet_lane_words": lw.value}
+
+
+def sw_last_host_stats() -> dict:
+    v = [ctypes.c_double() for _ in range(5)]
+    lib().sw_last_host_stats(*[ctypes.byref(x) for x in v])
+    return dict(zip(("stage_ms", "plan_ms", "post_ms", "table_ms", "gap_ms"), (x.value for x in v)))
 
 
 def sw_last_reduce_stats() -> dict:

@@ -19,7 +19,7 @@ def test_tune_small_grid():
     grid = {"set_cost": [512.0, 131072.0], "reduce": [0, 2], "dir_rule": [0, 1]}
     before = sw.sw_get_options()
     res = autotune.tune(sample, sw.workspace(1 << 30), grid=grid, repeats=1)
-    assert len(res["trials"]) == 8
+    assert len(res["trials"]) + res["pruned"] == 8 and res["complete"]
     assert res["best"] in [{k: t[k] for k in grid} for t in res["trials"]]
     after = sw.sw_get_options()  # the caller's options are restored
     assert (after.set_cost, after.reduce, after.dir_rule) == (before.set_cost, before.reduce, before.dir_rule)
