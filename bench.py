@@ -59,12 +59,12 @@ SM_MAX_MHZ_FALLBACK = 2070.0
 N_SMS_NOMINAL = 152
 # DRAM bytes (read + write) of the meet kernel per backward row it
 # transposes, from an ncu capture (dram__bytes_read.sum +
-# dram__bytes_write.sum) of single meet launches of the first 512 automata
-# of this workload; the full workload is too large for a multi-pass
-# capture, so its traffic per launch is this figure times the rows one
-# launch transposes (profiles/meet_traffic_batch512_c3.md; recaptured
-# whenever the kernel changes).
-MEET_DRAM_BYTES_PER_ROW = 13.4
+# dram__bytes_write.sum) of the meet launches of one step of the first 512
+# automata of this workload; the full workload is too large for a
+# multi-pass capture, so its traffic per launch is this figure times the
+# rows one launch transposes (profiles/meet_traffic_batch512_c3.md;
+# recaptured whenever the kernel changes).
+MEET_DRAM_BYTES_PER_ROW = 13.47
 
 
 def rank_seeds(rank: int, count: int) -> range:

@@ -1050,6 +1050,9 @@ struct Engine {
         RehashSeg *d_segs = nullptr;
         MarkJob *d_mark = nullptr;
         int64_t *d_mark_nt = nullptr;
+        FillJob *fills = nullptr;      // host side of the fills and rehash segments
+        RehashSeg *segs = nullptr;
+        std::vector<int> fill_owner;   // instance of each fill
     };
     // Word jobs staged with an iteration's jobs; their results are read
     // back with that iteration's level sizes.
@@ -1071,9 +1074,8 @@ struct Engine {
     std::vector<int> met_ids;
     std::vector<unsigned long long> met_best;
 
-    // Builds the job arrays of `sel` in the staging buffer (without the
-    // upload).  A step of an instance that is no longer active gets empty
-    // jobs: no candidates and no meet tiles.
+    // Builds the job arrays of `sel` (steps of active instances) in the
+    // staging buffer, without the upload.
     int build_stage(std::vector<Sel> &sel, Staged &S) {
         S = Staged{};
         if (!stage_begin()) return SW_ECUDA;
@@ -1093,7 +1095,7 @@ struct Engine {
             ExpandJob &J = jobs[t];
             J.cand_off = cand;
             J.parent_off = P.off;
-            J.parent_cnt = x.state == kActive ? P.cnt : 0;
+            J.parent_cnt = P.cnt;
             J.delta_off = x.delta_off;
             J.dest_off = s.dest;
             J.tab_off = rdir[s.d] ? s.new_tab : x.tab_off[s.d];
@@ -1106,9 +1108,11 @@ struct Engine {
             cand += round_up(s.nc, kScanBlock);
             if (rdir[s.d]) {
                 fills.push_back({s.new_tab, s.new_cap});
+                S.fill_owner.push_back(s.id);
                 S.maxfill = std::max(S.maxfill, s.new_cap);
             } else if (s.new_tab >= 0) {
                 fills.push_back({s.new_tab, s.new_cap});
+                S.fill_owner.push_back(s.id);
                 S.maxfill = std::max(S.maxfill, s.new_cap);
                 for (auto &l : x.lev[s.d]) {
                     segs.push_back({S.rehash_total, l.off, l.cnt, s.new_tab, s.new_cap, s.d, s.id});
@@ -1120,11 +1124,11 @@ struct Engine {
         S.nfill = (int)fills.size();
         S.nsegs = (int)segs.size();
         if (!fills.empty()) {
-            FillJob *f = stg.take<FillJob>(fills.size(), &S.d_fill);
-            RehashSeg *g = stg.take<RehashSeg>(std::max<size_t>(segs.size(), 1), &S.d_segs);
+            S.fills = stg.take<FillJob>(fills.size(), &S.d_fill);
+            S.segs = stg.take<RehashSeg>(std::max<size_t>(segs.size(), 1), &S.d_segs);
             if (!stg.ok) return SW_EINTERNAL;
-            std::memcpy(f, fills.data(), fills.size() * sizeof(FillJob));
-            if (!segs.empty()) std::memcpy(g, segs.data(), segs.size() * sizeof(RehashSeg));
+            std::memcpy(S.fills, fills.data(), fills.size() * sizeof(FillJob));
+            if (!segs.empty()) std::memcpy(S.segs, segs.data(), segs.size() * sizeof(RehashSeg));
         }
         // inclusion reductions: per job a self-reduction job over its own
         // candidates and one job per kept level of its direction (the
@@ -1163,7 +1167,7 @@ struct Engine {
             };
             for (int t = 0; t < nj; ++t) {
                 const Sel &sl = sel[t];
-                if (!rdir[sl.d] || jobs[t].parent_cnt == 0) continue;
+                if (!rdir[sl.d]) continue;
                 const Inst &x = I[sl.id];
                 const int64_t co = jobs[t].cand_off, cn = sl.nc;
                 if (sl.d == 0) {
@@ -1217,16 +1221,59 @@ struct Engine {
             M.ge_off = s.d == 1 ? s.ge : x.lev[1].back().ge;
             M.upd = s.d;
             M.count_idx = t;
-            if (jobs[t].parent_cnt == 0) empty_meet(M);
         }
         return SW_OK;
     }
 
-    // A meet job with no tiles (its instance met or failed after the step was planned).
-    static void empty_meet(MeetJob &M) {
-        M.f_cnt = 0;
-        M.b_cnt = 0;
-        M.upd = -1;
+    // Drops from staged jobs of a plain search, and from `sel`, the steps of
+    // instances that are no longer active (they met or failed after the step
+    // was planned; the memory planned for it stays with the instance until
+    // it ends).  The other jobs keep their order, with candidate ranges,
+    // level counts and rehash offsets renumbered.
+    void drop_inactive(std::vector<Sel> &sel, Staged &S) {
+        int w = 0;
+        int64_t cand = 0;
+        for (int t = 0; t < S.nj; ++t) {
+            const Sel s = sel[t];
+            if (I[s.id].state != kActive) {
+                planned[s.id] = 0;
+                continue;
+            }
+            ExpandJob J = S.jobs[t];
+            J.cand_off = cand;
+            cand += round_up(s.nc, kScanBlock);
+            MeetJob M = S.mj[t];
+            M.slot = w;
+            M.count_idx = w;
+            S.jobs[w] = J;
+            S.mj[w] = M;
+            sel[w] = s;
+            ++w;
+        }
+        sel.resize((size_t)w);
+        S.nj = w;
+        S.ncand = cand;
+        int f = 0;
+        S.maxfill = 1;
+        for (int t = 0; t < S.nfill; ++t) {
+            if (I[S.fill_owner[t]].state != kActive) continue;
+            S.fills[f] = S.fills[t];
+            S.fill_owner[f] = S.fill_owner[t];
+            S.maxfill = std::max(S.maxfill, S.fills[f].len);
+            ++f;
+        }
+        S.nfill = f;
+        int g = 0;
+        int64_t total = 0;
+        for (int t = 0; t < S.nsegs; ++t) {
+            if (I[S.segs[t].inst].state != kActive) continue;
+            RehashSeg r = S.segs[t];
+            r.flat_off = total;
+            total += r.cnt;
+            S.segs[g++] = r;
+        }
+        S.nsegs = g;
+        S.rehash_total = total;
     }
 
     // Stages word jobs for met[pos ..] (as many as the staging buffer holds;
@@ -1341,7 +1388,7 @@ struct Engine {
     // finds are recovered at the start of the next iteration, ahead of its
     // expansion (so the device goes from one meet to the next expansion
     // without waiting for the host), and end with that iteration's level
-    // sizes; a step staged for an instance that met is emptied.
+    // sizes; a step staged for an instance that met is dropped.
     int iterate() {
         g_stats.iterations++;
         auto t_sel = std::chrono::steady_clock::now();
@@ -1356,7 +1403,11 @@ struct Engine {
         if (use_pre)
             for (int id : active)
                 if (!planned[id]) use_pre = false;
-        if (!use_pre) {
+        Staged S;
+        if (use_pre) {
+            S = pre;
+            drop_inactive(sel, S);
+        } else {
             // steps planned for instances that have since met or failed go,
             // with their memory (kept by the instance until it ends)
             sel.erase(std::remove_if(sel.begin(), sel.end(),
@@ -1394,15 +1445,7 @@ struct Engine {
             }
             return SW_OK;
         }
-        Staged S;
-        if (use_pre) {
-            S = pre;
-            for (int t = 0; t < S.nj; ++t)
-                if (I[sel[t].id].state != kActive) {
-                    S.jobs[t].parent_cnt = 0;
-                    empty_meet(S.mj[t]);
-                }
-        } else {
+        if (!use_pre) {
             int rc = build_stage(sel, S);
             if (rc) return rc;
         }
@@ -1515,7 +1558,7 @@ struct Engine {
             std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t_upd).count();
         // plan (and for a plain search stage) the next iteration while the
         // meet kernel runs; a step planned for an instance that meets now is
-        // emptied or dropped next time
+        // dropped next time
         auto t_plan = std::chrono::steady_clock::now();
         plan(pending);
         if (!pending.empty() && !rdir[0] && !rdir[1]) {
