@@ -261,6 +261,15 @@ int32_t sw_last_stats(int64_t *pairs, int64_t *candidates, int32_t *iterations,
                       int32_t *meet_lane_words);
 
 /*
+ * Counters of the calling thread's last search's memory-bounded inverse
+ * phase (sw_options.dfs_sets, Section 2.2): instances that ran it, chunks
+ * of roots it expanded (each to its full depth), and sets it made (after
+ * the duplicates of each chunk and depth).  Any pointer may be NULL.
+ * Returns SW_OK.
+ */
+int32_t sw_last_dfs_stats(int64_t *instances, int64_t *chunks, int64_t *sets);
+
+/*
  * Where the calling thread's last search spent the time between kernels
  * (no counterpart in the paper; the device figures need sw_set_timing(1)).
  *   stage_ms:  host time building and uploading each iteration's jobs, from
@@ -364,6 +373,22 @@ void sw_set_timing(int32_t on);
  *                         estimate with the lists' densities (eq. 1 and 4).
  *                         The schedule never changes r, the word or the
  *                         level sizes.
+ *   dfs_sets:             the memory-bounded inverse phase (Section 2.2,
+ *                         built breadth-first per chunk instead of as a
+ *                         depth-first recursion): 0 (default) off, an
+ *                         instance whose next step does not fit ends with
+ *                         SW_ENOMEM; -1 on when no step of the last active
+ *                         instance fits; n > 0 also once an instance's
+ *                         stored sets plus its next step's candidates would
+ *                         exceed n.  The last forward level F_i stays fixed;
+ *                         the last backward level B_j is cut into chunks
+ *                         that are expanded D = 1, 2, ... inverse steps deep
+ *                         (duplicates removed per chunk and depth, no
+ *                         history) and checked against F_i; the first D with
+ *                         a meet gives r = i + j + D.  r is exact; the word
+ *                         is a reset word of length r, not necessarily the
+ *                         least one; sw_level_sizes reports the levels of
+ *                         the bidirectional phase only.
  * Applies to later searches on the calling thread.
  */
 typedef struct sw_options {
@@ -377,6 +402,7 @@ typedef struct sw_options {
     int32_t reduce;
     int32_t table_cap_slots;
     int32_t dir_rule;
+    int64_t dfs_sets;
 } sw_options;
 
 void sw_get_options(sw_options *opt);

@@ -56,12 +56,13 @@ struct Stats {
     double stage_ms = 0, plan_ms = 0, post_ms = 0;  // host: job staging, planning during the meet, after the meet
     double table_ms = 0;     // device: job upload, table fills and rehash before each expansion
     double gap_ms = 0;       // device: from a meet's end to the next iteration's job upload
+    int64_t dfs_instances = 0, dfs_chunks = 0, dfs_sets = 0;  // inverse phase: instances, chunks, sets made
     double mark_ms = 0;      // inclusion reductions: device time of the marking kernel
     int64_t mark_pairs = 0, mark_steps = 0, mark_rows = 0;  // its pairs, AND steps, rows transposed
 };
 
 thread_local int32_t g_last_error = SW_OK;
-thread_local sw_options g_opt = {0, 0, 0, 4096, 0, 1.0, 8192.0, 0, 0, 0};
+thread_local sw_options g_opt = {0, 0, 0, 4096, 0, 1.0, 8192.0, 0, 0, 0, 0};
 thread_local bool g_timing = false;
 thread_local Stats g_stats;
 // Set only while sw_reset_threshold_static runs: staging buffers then come
@@ -201,8 +202,9 @@ struct Pool {
 
 // ---------------------------------------------------------------- per-instance state
 
-// kMet: a meet was found and the word is still being recovered
-enum InstState { kWaiting = 0, kActive = 1, kDone = 2, kFailed = 3, kMet = 4 };
+// kMet: a meet was found and the word is still being recovered; kDfs:
+// waiting for the memory-bounded inverse phase
+enum InstState { kWaiting = 0, kActive = 1, kDone = 2, kFailed = 3, kMet = 4, kDfs = 5 };
 
 struct Level {
     int64_t off, cnt, cap;  // arena index, sets, slots reserved
@@ -1034,6 +1036,15 @@ struct Engine {
             // a step that does not fit in memory counts as infinitely
             // expensive (Section 2.1.2), so the other direction is tried
             const int d = choose_dir(I[id]);
+            if (g_opt.dfs_sets > 0) {
+                // past the set budget the instance goes on with the inverse phase
+                const Inst &x = I[id];
+                if (x.stored[0] + x.stored[1] + x.k * x.lev[d].back().cnt > g_opt.dfs_sets) {
+                    I[id].state = kDfs;
+                    dfs_ids.push_back(id);
+                    continue;
+                }
+            }
             if (!try_step(id, d)) try_step(id, 1 - d);
         }
     }
@@ -1382,6 +1393,244 @@ struct Engine {
         return SW_OK;
     }
 
+    // ------------------------------------------------------------ DFS phase
+
+    // Instances waiting for the memory-bounded inverse phase (state kDfs).
+    std::vector<int> dfs_ids;
+
+    // Runs the inverse phase of every waiting instance, one at a time.
+    int run_dfs_pending() {
+        std::vector<int> ids;
+        ids.swap(dfs_ids);
+        for (int id : ids) {
+            if (I[id].state != kDfs) continue;  // its last meet found it first
+            int rc = dfs_phase(id);
+            if (rc) return rc;
+        }
+        return SW_OK;
+    }
+
+    // One chunk of the inverse phase: the roots B_j[c0, c0 + cs) are expanded
+    // D inverse steps deep (duplicates removed per depth, in a table of each
+    // expansion's own), and the depth-D sets are checked against F_i.
+    // Returns SW_OK with *found set when they meet (the word is then
+    // recovered and the instance ends), kDfsRetry when the chunk does not
+    // fit (the caller halves it), or an error.
+    static constexpr int kDfsRetry = -1;
+    int dfs_chunk(Inst &x, int id, const Level &F, const Level &B, int64_t c0, int64_t cs, int D, bool *found) {
+        *found = false;
+        std::vector<Level> T;
+        std::vector<std::pair<int64_t, int64_t>> set_allocs, tab_allocs;
+        auto release_all = [&]() {
+            for (auto &a : set_allocs) set_pool.release(a.first, a.second);
+            for (auto &a : tab_allocs) tab_pool.release(a.first, a.second);
+        };
+        T.push_back({B.off + c0, cs, cs, -1});
+        uint64_t *down = (uint64_t *)g_down.get(8 * sizeof(uint64_t));
+        if (!down) return SW_ECUDA;
+        for (int e = 1; e <= D; ++e) {
+            const Level P = T.back();
+            const int64_t nc = x.k * P.cnt;
+            const int64_t ncp = round_up(nc, kScanBlock);
+            if (ncp > L.cap_cand) {
+                release_all();
+                return kDfsRetry;
+            }
+            const int64_t tcap = capped_slots(round_up(2 * nc + 64, 64));
+            const int64_t gs = set_pool.alloc(ge_slots());
+            const int64_t dest = gs >= 0 ? set_pool.alloc(nc) : -1;
+            const int64_t tab = dest >= 0 ? tab_pool.alloc(tcap) : -1;
+            if (gs >= 0) set_allocs.push_back({gs, ge_slots()});
+            if (dest >= 0) set_allocs.push_back({dest, nc});
+            if (tab >= 0) tab_allocs.push_back({tab, tcap});
+            if (tab < 0) {
+                release_all();
+                return kDfsRetry;
+            }
+            if (!stage_begin()) return SW_ECUDA;
+            ExpandJob *d_job = nullptr;
+            FillJob *d_fill = nullptr;
+            ExpandJob *J = stg.take<ExpandJob>(1, &d_job);
+            FillJob *fj = stg.take<FillJob>(1, &d_fill);
+            if (!stg.ok) return SW_EINTERNAL;
+            *J = ExpandJob{};
+            J->cand_off = 0;
+            J->parent_off = P.off;
+            J->parent_cnt = P.cnt;
+            J->delta_off = x.delta_off;
+            J->dest_off = dest;
+            J->tab_off = tab;
+            J->tab_cap = tcap;
+            J->ge_off = gs * 2 * W;
+            J->dir = 1;
+            J->n = x.n;
+            J->k = x.k;
+            J->inst = id;
+            *fj = {tab, tcap};
+            int rc = stage_flush();
+            if (rc) return rc;
+            CK(ops.fill(d_fill, 1, tcap, L, st));
+            CK(ops.expand(d_job, 1, ncp, L, st));
+            CK(ops.compact(d_job, 1, ncp, 0, L, st));
+            CK(cudaMemcpyAsync(down, L.counts, sizeof(uint64_t), cudaMemcpyDeviceToHost, st));
+            CK(cudaMemcpyAsync(down + 1, L.status, sizeof(uint32_t), cudaMemcpyDeviceToHost, st));
+            CK(wait_stream(st));
+            g_stats.candidates += ncp;
+            g_stats.dfs_sets += (int64_t)down[0];
+            if ((uint32_t)(down[1] & 0xFFFFFFFFu) & kStatusTableFull) {
+                // probes ran out in this expansion's table: a smaller chunk
+                CK(cudaMemsetAsync(L.status, 0, (size_t)L.status_n * sizeof(uint32_t), st));
+                CK(wait_stream(st));
+                release_all();
+                return kDfsRetry;
+            }
+            const int64_t c = (int64_t)down[0];
+            T.push_back({dest, c, c, gs * 2 * W});
+            if (c == 0) {  // no preimage of this depth: the chunk cannot meet at depth D
+                release_all();
+                return SW_OK;
+            }
+        }
+        // the depth-D sets against F_i
+        const Level &TD = T.back();
+        if (!stage_begin()) return SW_ECUDA;
+        MeetJob *d_mj = nullptr;
+        MeetJob *M = stg.take<MeetJob>(1, &d_mj);
+        if (!stg.ok) return SW_EINTERNAL;
+        *M = MeetJob{};
+        M->f_off = F.off;
+        M->f_cnt = F.cnt;
+        M->b_off = TD.off;
+        M->b_cnt = TD.cnt;
+        M->tile_off = 0;
+        M->ntb = 1;
+        M->slot = 0;
+        M->ge_off = TD.ge;
+        M->upd = -1;
+        M->count_idx = 0;
+        int rc = stage_flush();
+        if (rc) return rc;
+        CK(cudaMemsetAsync(L.best, 0xFF, sizeof(unsigned long long), st));
+        CK(cudaMemsetAsync(L.pairs, 0, 3 * sizeof(unsigned long long), st));
+        CK(ops.meet(d_mj, 1, mc, mc.tf_rows, L, st));
+        CK(cudaMemcpyAsync(down + 2, L.best, sizeof(unsigned long long), cudaMemcpyDeviceToHost, st));
+        CK(cudaMemcpyAsync(down + 3, L.pairs, 3 * sizeof(unsigned long long), cudaMemcpyDeviceToHost, st));
+        CK(wait_stream(st));
+        g_stats.meet_launches++;
+        g_stats.pairs += (int64_t)down[3];
+        g_stats.and_iters += (int64_t)down[4];
+        g_stats.rows_transposed += (int64_t)down[5];
+        if (down[2] == ~0ull) {
+            release_all();
+            return SW_OK;
+        }
+        // a meet at depth D: the word runs through F_i's parent chain, then
+        // the chunk's levels T_{D-1} .. T_1 and the kept levels B_j .. B_0
+        *found = true;
+        const int i = (int)x.lev[0].size() - 1, j = (int)x.lev[1].size() - 1;
+        x.r = i + j + D;
+        if (!device_words && x.r > L.word_area_cap) {
+            release_all();
+            finish(x, kFailed, SW_ENOMEM);
+            return SW_OK;
+        }
+        if (!stage_begin()) return SW_ECUDA;
+        WordBatch wb;
+        WordJob Jw;
+        Jw.f_arena = F.off + (int64_t)(down[2] >> 32);
+        Jw.blev = 0;
+        Jw.word_off = device_words ? x.word_off : 0;
+        Jw.delta_off = x.delta_off;
+        Jw.i = i;
+        Jw.j = j + D;
+        Jw.n = x.n;
+        Jw.k = x.k;
+        Jw.slot = 0;
+        Jw.pad = id;
+        wb.wj.push_back(Jw);
+        if (!device_words) wb.area = x.r;
+        WordJob *hw = stg.take<WordJob>(1, &wb.d_wj);
+        int64_t *hb = stg.take<int64_t>(3 * (size_t)(j + D), &wb.d_bl);
+        if (!stg.ok) return SW_EINTERNAL;
+        *hw = Jw;
+        for (int m = 0; m <= j; ++m) {
+            hb[3 * m] = x.lev[1][m].off;
+            hb[3 * m + 1] = x.lev[1][m].cnt;
+            hb[3 * m + 2] = x.lev[1][m].ge;
+        }
+        for (int e = 1; e < D; ++e) {
+            hb[3 * (j + e)] = T[e].off;
+            hb[3 * (j + e) + 1] = T[e].cnt;
+            hb[3 * (j + e) + 2] = T[e].ge;
+        }
+        rc = stage_flush();
+        if (rc) return rc;
+        rc = launch_words(wb);
+        if (rc) return rc;
+        CK(wait_stream(st));
+        release_all();
+        collect_words(wb);
+        return SW_OK;
+    }
+
+    // The memory-bounded inverse phase of Section 2.2 for one instance.  The
+    // paper runs it as a depth-first recursion from each set of the last
+    // inverse level, checking every set it visits against the last forward
+    // level; here the same search runs breadth-first per chunk of roots,
+    // depth by depth (D = 1, 2, ...), so that each depth is one expansion
+    // launch over the whole chunk.  Correctness: a shortest reset word
+    // x y z with |x| = i and |z| = j has delta(Q, x) in F_i and
+    // delta^-1({q}, z) in B_j (both first reached at those depths, else a
+    // shorter word would exist), and delta^-1(delta^-1({q}, z), y) contains
+    // delta(Q, x); no smaller D can meet, for the same reason.
+    int dfs_phase(int id) {
+        Inst &x = I[id];
+        x.state = kActive;
+        g_stats.dfs_instances++;
+        // no bidirectional step follows: the hash tables go back to the pool
+        for (int d = 0; d < 2; ++d) {
+            if (x.tab_off[d] >= 0) tab_pool.release(x.tab_off[d], x.tab_cap[d]);
+            x.tab_off[d] = -1;
+            x.tab_cap[d] = 0;
+        }
+        const Level F = x.lev[0].back();
+        const Level B = x.lev[1].back();
+        const int i = (int)x.lev[0].size() - 1, j = (int)x.lev[1].size() - 1;
+        // r is at most (n^3 - n) / 6 (the Pin-Frankl bound) and the word cap
+        const double pf = ((double)x.n * x.n * x.n - x.n) / 6.0 + 1.0;
+        const int64_t rmax = (int64_t)std::min<double>({pf, (double)x.word_cap, 1e6});
+        const int64_t dmax = rmax - i - j;
+        for (int64_t D = 1; D <= dmax; ++D) {
+            // roots per chunk: the chunk's deepest level (at most k^D sets
+            // per root) must fit in the candidate buffer and in a quarter of
+            // the free set slots (and within dfs_sets when that is set)
+            double reach = std::pow((double)x.k, (double)D);
+            double room = std::min((double)L.cap_cand, 0.25 * (double)(set_pool.cap - set_pool.used));
+            if (g_opt.dfs_sets > 0) room = std::min(room, (double)g_opt.dfs_sets);
+            int64_t cs = (int64_t)std::min<double>((double)B.cnt, std::floor(room / reach));
+            if (cs < 1) cs = 1;
+            for (int64_t c0 = 0; c0 < B.cnt;) {
+                const int64_t n_here = std::min(cs, B.cnt - c0);
+                bool found = false;
+                int rc = dfs_chunk(x, id, F, B, c0, n_here, (int)D, &found);
+                if (rc == kDfsRetry) {
+                    if (n_here == 1) {  // not even one root fits
+                        finish(x, kFailed, SW_ENOMEM);
+                        return SW_OK;
+                    }
+                    cs = std::max<int64_t>(1, n_here / 2);
+                    continue;
+                }
+                if (rc) return rc;
+                g_stats.dfs_chunks++;
+                if (found) return SW_OK;  // the instance has ended
+                c0 += n_here;
+            }
+        }
+        finish(x, kFailed, SW_EWORDCAP);
+        return SW_OK;
+    }
+
     // One iteration over the active instances.  The next iteration's steps
     // are planned, and for a plain search staged, on the host while this
     // iteration's meet kernel runs.  The words of the instances that meet
@@ -1396,6 +1645,10 @@ struct Engine {
         // objects: it waits for the whole stream instead of a counts event
         const bool counts_event = !g_pageable;
         if (counts_event && !ev_counts) CK(cudaEventCreateWithFlags(&ev_counts, cudaEventDisableTiming));
+        if (!dfs_ids.empty()) {
+            int rc = run_dfs_pending();
+            if (rc) return rc;
+        }
         std::vector<Sel> sel;
         sel.swap(pending);
         // the staged jobs serve when every active instance has its step in them
@@ -1427,6 +1680,11 @@ struct Engine {
             met_ids.clear();
             met_best.clear();
             if (rc) return rc;
+            // instances just sent to the inverse phase leave the active set and run it now
+            active.erase(std::remove_if(active.begin(), active.end(), [&](int a) { return I[a].state != kActive; }),
+                         active.end());
+            rc = run_dfs_pending();
+            if (rc) return rc;
             if (active.empty()) return SW_OK;
             // nothing fits: set back the instance holding the most memory
             auto it = std::max_element(active.begin(), active.end(),
@@ -1436,7 +1694,12 @@ struct Engine {
             Inst &x = I[id];
             g_stats.evictions++;
             if (active.empty()) {  // it had all the room there is
-                finish(x, kFailed, SW_ENOMEM);
+                if (g_opt.dfs_sets != 0 && x.state == kActive) {
+                    int rc = dfs_phase(id);
+                    if (rc) return rc;
+                } else {
+                    finish(x, kFailed, SW_ENOMEM);
+                }
             } else {
                 release(x);
                 x.state = kWaiting;
@@ -1602,7 +1865,8 @@ struct Engine {
         g_stats.rows_transposed += (int64_t)d_pairs[2];
         for (int t = 0; t < nj; ++t) {
             Inst &x = I[sel[t].id];
-            if (x.state != kActive || d_best[t] == ~0ull) continue;
+            // an instance sent to the inverse phase while this meet ran keeps its meet
+            if ((x.state != kActive && x.state != kDfs) || d_best[t] == ~0ull) continue;
             x.state = kMet;
             met_ids.push_back(sel[t].id);
             met_best.push_back(d_best[t]);
@@ -1622,6 +1886,8 @@ struct Engine {
                 if (rdir[s.d]) tab_pool.release(s.new_tab, s.new_cap);
             }
             pending.clear();
+            rc = run_dfs_pending();
+            if (rc) return rc;
         }
         g_stats.arena_peak = std::max(g_stats.arena_peak, set_pool.used);
         g_stats.post_ms +=
@@ -2199,6 +2465,7 @@ void sw_set_options(const sw_options *opt) {
     if (g_opt.reduce < 0 || g_opt.reduce > 3) g_opt.reduce = 0;
     if (g_opt.table_cap_slots < 0) g_opt.table_cap_slots = 0;
     if (g_opt.dir_rule != 1) g_opt.dir_rule = 0;
+    if (g_opt.dfs_sets < -1) g_opt.dfs_sets = 0;
 }
 
 double sw_expmark(double a_s, double b_s, double a_d, double b_d) { return expmark(a_s, b_s, a_d, b_d); }
@@ -2209,6 +2476,13 @@ int32_t sw_last_host_stats(double *stage_ms, double *plan_ms, double *post_ms, d
     if (post_ms) *post_ms = g_stats.post_ms;
     if (table_ms) *table_ms = g_stats.table_ms;
     if (gap_ms) *gap_ms = g_stats.gap_ms;
+    return SW_OK;
+}
+
+int32_t sw_last_dfs_stats(int64_t *instances, int64_t *chunks, int64_t *sets) {
+    if (instances) *instances = g_stats.dfs_instances;
+    if (chunks) *chunks = g_stats.dfs_chunks;
+    if (sets) *sets = g_stats.dfs_sets;
     return SW_OK;
 }
 

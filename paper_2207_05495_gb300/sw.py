@@ -36,7 +36,7 @@ class sw_options(ctypes.Structure):
                 ("meet_b_tile", ctypes.c_int32), ("meet_f_rows", ctypes.c_int32),
                 ("meet_lane_words", ctypes.c_int32),
                 ("dir_theta", ctypes.c_double), ("set_cost", ctypes.c_double), ("reduce", ctypes.c_int32),
-                ("table_cap_slots", ctypes.c_int32), ("dir_rule", ctypes.c_int32)]
+                ("table_cap_slots", ctypes.c_int32), ("dir_rule", ctypes.c_int32), ("dfs_sets", ctypes.c_int64)]
 
 
 def lib():
@@ -77,6 +77,8 @@ def lib():
         L.sw_last_reduce_stats.restype = i32
         L.sw_last_host_stats.argtypes = [p] * 5
         L.sw_last_host_stats.restype = i32
+        L.sw_last_dfs_stats.argtypes = [p] * 3
+        L.sw_last_dfs_stats.restype = i32
         L.sw_set_timing.argtypes = [i32]
         L.sw_set_timing.restype = None
         L.sw_get_options.argtypes = [p]
@@ -253,6 +255,7 @@ def sw_last_stats() -> dict:
     d = _last_stats()
     d.update(sw_last_reduce_stats())
     d.update(sw_last_host_stats())
+    d.update(sw_last_dfs_stats())
     return d
 
 
@@ -281,6 +284,12 @@ def sw_last_host_stats() -> dict:
     v = [ctypes.c_double() for _ in range(5)]
     lib().sw_last_host_stats(*[ctypes.byref(x) for x in v])
     return dict(zip(("stage_ms", "plan_ms", "post_ms", "table_ms", "gap_ms"), (x.value for x in v)))
+
+
+def sw_last_dfs_stats() -> dict:
+    v = [ctypes.c_int64() for _ in range(3)]
+    lib().sw_last_dfs_stats(*[ctypes.byref(x) for x in v])
+    return dict(zip(("dfs_instances", "dfs_chunks", "dfs_sets"), (x.value for x in v)))
 
 
 def sw_last_reduce_stats() -> dict:

@@ -96,3 +96,26 @@ def test_expmark_cost_estimate(lib):
     sparse = sw.sw_expmark(1e6, 10, 1e-6, 0.5) / sw.sw_expmark(1e5, 10, 1e-6, 0.5)
     assert 9.9 < sparse < 10.0
     assert sw.sw_expmark(0, 10, 0.1, 0.5) == 0.0
+
+
+def test_options_round_trip_and_clamp(lib):
+    # the struct layout matches the library's (the last field survives a
+    # round trip) and out-of-range values are clamped on the host
+    old = sw.sw_get_options()
+    try:
+        o = sw.sw_get_options()
+        o.dfs_sets = 12345
+        o.dir_rule = 1
+        sw.sw_set_options(o)
+        got = sw.sw_get_options()
+        assert (got.dfs_sets, got.dir_rule) == (12345, 1)
+        o.dfs_sets = -7
+        o.reduce = 9
+        sw.sw_set_options(o)
+        got = sw.sw_get_options()
+        assert (got.dfs_sets, got.reduce) == (0, 0)
+        o.dfs_sets = -1
+        sw.sw_set_options(o)
+        assert sw.sw_get_options().dfs_sets == -1
+    finally:
+        sw.sw_set_options(old)
