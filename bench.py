@@ -794,6 +794,8 @@ def run_hard(args, d, cfg, sw, torch, local, world, peak, nsm):
                  "pairs_per_s_in_meet_kernel": pairs / (meet_ms * 1e-3) if meet_ms > 0 else None,
                  "meet_ms": meet_ms, "expand_ms": st["expand_ms"], "compact_ms": st["compact_ms"],
                  "mark_ms": st["mark_ms"], "mark_pairs": st["mark_pairs"],
+                 "inverse_phase": {"ran": bool(st["dfs_instances"]), "chunks": st["dfs_chunks"],
+                                   "sets": st["dfs_sets"], "depth": r - (len(fs) - 1) - (len(bs) - 1)},
                  "balanced_schedule": {"r": r2, "seconds": sec2, "peak_sets": st2["arena_peak"],
                                        "pairs": st2["pairs"], "fwd_levels": len(fs2) - 1,
                                        "bwd_levels": len(bs2) - 1},
