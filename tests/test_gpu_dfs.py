@@ -147,3 +147,24 @@ def test_memory_exhausted(sw, restore):
             assert check(sw, d, h, r, w)
             seen += 1
     assert seen >= 1
+
+
+@pytest.mark.parametrize("reduce_mode", [1, 2, 3], ids=["both", "bfs", "ibfs"])
+def test_after_reduced_phase(sw, ws, restore, reduce_mode):
+    # the inverse phase after a reduced bidirectional phase: F_i and B_j
+    # hold a subset (superset) of every set first reached at their depths,
+    # so r is still the oracle's; the word resets and has length r
+    o = sw.sw_get_options()
+    o.reduce = reduce_mode
+    o.dfs_sets = 40
+    sw.sw_set_options(o)
+    ran = 0
+    for seed in range(8):
+        d = gen.random_automaton(36, 2, 6200 + seed)
+        h = sw.load(d)
+        r, w = sw.sw_reset_threshold(h, ws=ws)
+        assert r == oracle.bidir(d)[0]
+        assert len(w) == r and resets(d, w)
+        fs, bs = sw.sw_level_sizes(h)
+        ran += len(fs) + len(bs) - 2 < r
+    assert ran >= 1
