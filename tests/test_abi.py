@@ -119,3 +119,28 @@ def test_options_round_trip_and_clamp(lib):
         assert sw.sw_get_options().dfs_sets == -1
     finally:
         sw.sw_set_options(old)
+
+
+def test_every_declaration_is_documented():
+    # each entry point of the header has a comment block (what it computes,
+    # with the paper's passage where one applies, and argument layout,
+    # ownership and errors) ending at most 25 lines above its declaration;
+    # a block may serve a group of declarations, a typedef or a #define
+    text = open(os.path.join(ROOT, "include", "sw.h")).read()
+    lines = text.splitlines()
+    in_comment = False
+    undocumented = []
+    last_comment_end = -10**9
+    for i, line in enumerate(lines):
+        st = line.strip()
+        if st.startswith("/*"):
+            in_comment = True
+        if in_comment:
+            if st.endswith("*/"):
+                in_comment = False
+                last_comment_end = i
+            continue
+        m = re.match(r"^[A-Za-z_][\w\s\*]*?\b(sw_[a-z_]+)\s*\(", line)
+        if m and i - last_comment_end > 25:
+            undocumented.append(m.group(1))
+    assert not undocumented, undocumented
