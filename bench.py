@@ -733,6 +733,19 @@ def tensor_core_pairs_per_s(torch, K: int, M: int = 16384, N: int = 16384):
         return {"gemm": "torch._scaled_mm e4m3", "unavailable": str(e)[:200]}
 
 
+def schedules_agree(a, b, words_unique: bool) -> bool:
+    """Whether two searches of one automaton under different direction
+    schedules agree: a and b are (r, word, forward sizes, backward sizes).
+    r and the sizes of every level both computed must be equal; the words
+    must be equal only when the search returns a unique word (the plain
+    search's least word), not with a reduced side or the inverse phase,
+    whose word depends on where the searches met."""
+    r, w, fs, bs = a
+    r2, w2, fs2, bs2 = b
+    m_, mb = min(len(fs), len(fs2)), min(len(bs), len(bs2))
+    return r == r2 and fs[:m_] == fs2[:m_] and bs[:mb] == bs2[:mb] and (w == w2 or not words_unique)
+
+
 def run_hard(args, d, cfg, sw, torch, local, world, peak, nsm):
     """A hard single instance: W warm-up and K timed searches with the
     library's direction rule, then one with "expand the smaller side"
@@ -775,9 +788,9 @@ def run_hard(args, d, cfg, sw, torch, local, world, peak, nsm):
     states = np.arange(n)
     for a in w:
         states = d[a][states]
-    m_ = min(len(fs), len(fs2))
-    mb = min(len(bs), len(bs2))
-    agree = (r, w) == (r2, w2) and fs[:m_] == fs2[:m_] and bs[:mb] == bs2[:mb]
+    opts = sw.sw_get_options()
+    agree = schedules_agree((r, w, fs, bs), (r2, w2, fs2, bs2),
+                            words_unique=opts.reduce == 0 and opts.dfs_sets == 0)
     meet_ms, pairs, iters, rows_t, launches, lw = meet_roofline([x[3] for x in runs], nsm)
     W = (n + 63) // 64
     ops = iters * 64 * lw + rows_t * 2 * W * 25

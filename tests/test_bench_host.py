@@ -105,3 +105,16 @@ def test_reference_arm_large_beam_is_unavailable():
 def test_workloads_beam_shape():
     ds, cfg = bench.workload("beam5000")
     assert len(ds) == 1 and ds[0].shape == (2, 5000) and "beam n*ceil(log2 n) = 65000" in cfg["workload"]
+
+
+def test_schedules_agree_words_only_when_unique():
+    a = (5, [0, 1, 1, 0, 1], [1, 2, 3], [4, 6])
+    same_sizes_other_word = (5, [1, 0, 1, 1, 0], [1, 2, 3, 5], [4])
+    assert bench.schedules_agree(a, a, True)
+    # another reset word of length r: a disagreement for the plain search
+    # (its word is the least one), not with a reduced side or the inverse phase
+    assert not bench.schedules_agree(a, same_sizes_other_word, True)
+    assert bench.schedules_agree(a, same_sizes_other_word, False)
+    # r or a level both computed that differ: never an agreement
+    assert not bench.schedules_agree(a, (6,) + a[1:], False)
+    assert not bench.schedules_agree(a, (5, a[1], [1, 2, 4], [4, 6]), False)
