@@ -41,6 +41,12 @@
  *                          an inverse BFS that keeps only the `beam`
  *                          largest preimages of every depth (the cut-off
  *                          inverse BFS the paper cites).
+ *   oracle_inverse_dfs_r   Section 2.2: r from the last levels F_i, B_j of a
+ *                          bidirectional search by the inverse DFS phase (a
+ *                          depth-first search over preimages from every set
+ *                          of B_j, no history, each set reached checked
+ *                          against F_i by brute force), deepened one step at
+ *                          a time.
  *   oracle_is_synchronizing  Section 2, first step: every pair of states can
  *                          be mapped to one state.
  *
@@ -877,6 +883,89 @@ int oracle_beam(int n, int k, const int32_t *delta, int64_t beam, int32_t max_de
     }
     for (int d = 0; d < cap; d++) level_free(&lv[d]);
     free(lv);
+    return rc;
+}
+
+/* ------------------------------------------------------------------ */
+/* O5: the inverse DFS phase (Section 2.2)                              */
+/* ------------------------------------------------------------------ */
+
+/* The level of one direction at depth `depth` (distinct sets first reached
+ * there, as oracle_level_sizes counts them), left in *out. */
+static int level_at(int n, int k, const int32_t *delta, int dir, int depth, int64_t max_sets, level_t *out) {
+    int W = words_for(n);
+    level_t cur = {0}, next = {0};
+    history_t H = {0, NULL};
+    int rc = dir == 0 ? level_root_Q(&cur, n, W) : level_root_singletons(&cur, n, W);
+    if (!rc) rc = history_init(&H, &cur, n, W);
+    int64_t stored = cur.count;
+    for (int d = 1; !rc && d <= depth; d++) {
+        rc = expand(n, k, delta, dir, &cur, &H, &next, max_sets - stored);
+        if (rc) break;
+        stored += next.count;
+        if (stored > max_sets) rc = OR_ETOOBIG;
+        level_t t = cur; cur = next; next = t;
+    }
+    level_free(&next);
+    free(H.sets);
+    if (rc) level_free(&cur);
+    else *out = cur;
+    return rc;
+}
+
+/* Some X of F lies inside Y (brute force over F: the query the paper's
+ * static trie answers). */
+static int some_subset(const level_t *F, const uint64_t *Y, int n, int W) {
+    for (int64_t f = 0; f < F->count; f++)
+        if (set_subset(F->sets + f * W, Y, n)) return 1;
+    return 0;
+}
+
+/* Depth-first over the preimages of Y, d more inverse steps: 1 when a set
+ * reached after exactly d steps contains a set of F.  buf holds one set
+ * per remaining step. */
+static int dfs_reaches(int n, int k, const int32_t *delta, const level_t *F, const uint64_t *Y, int d,
+                       uint64_t *buf, int W) {
+    if (d == 0) return some_subset(F, Y, n, W);
+    uint64_t *P = buf;
+    for (int a = 0; a < k; a++) {
+        set_preimage(n, delta + (size_t)a * n, Y, P, W);
+        if (set_first(P, n) < 0) continue; /* empty preimage */
+        if (dfs_reaches(n, k, delta, F, P, d - 1, buf + W, W)) return 1;
+    }
+    return 0;
+}
+
+/*
+ * r from the last levels F_i (BFS) and B_j (IBFS) of a bidirectional
+ * search, by the memory-bounded inverse phase of Section 2.2: a depth-first
+ * inverse search from every set of B_j, without history, checking the sets
+ * it reaches against F_i.  D is deepened one step at a time (D = 0, 1, ...,
+ * D = 0 being the meet of F_i and B_j themselves); the first D at which some
+ * set of B_j reaches, after exactly D inverse steps, a superset of a set of
+ * F_i gives r = fwd_depth + bwd_depth + D.  Returns OR_ENOTFOUND when no D up
+ * to max_depth does.
+ */
+int oracle_inverse_dfs_r(int n, int k, const int32_t *delta, int32_t fwd_depth, int32_t bwd_depth,
+                         int32_t max_depth, int64_t max_sets, int32_t *r_out) {
+    int rc = check_automaton(n, k, delta);
+    if (rc) return rc;
+    if (fwd_depth < 0 || bwd_depth < 0 || max_depth < 0 || !r_out || n > 1024) return OR_EINVAL;
+    int W = words_for(n);
+    level_t F = {0}, B = {0};
+    rc = level_at(n, k, delta, 0, fwd_depth, max_sets, &F);
+    if (!rc) rc = level_at(n, k, delta, 1, bwd_depth, max_sets, &B);
+    uint64_t *buf = rc ? NULL : (uint64_t *)malloc((size_t)(max_depth + 1) * W * sizeof(uint64_t));
+    if (!rc && !buf) rc = OR_ENOMEM;
+    int found = -1;
+    for (int D = 0; !rc && found < 0 && D <= max_depth; D++)
+        for (int64_t b = 0; found < 0 && b < B.count; b++)
+            if (dfs_reaches(n, k, delta, &F, B.sets + b * W, D, buf, W)) found = D;
+    if (!rc && found < 0) rc = OR_ENOTFOUND;
+    if (!rc) *r_out = fwd_depth + bwd_depth + found;
+    free(buf);
+    level_free(&F);
+    level_free(&B);
     return rc;
 }
 

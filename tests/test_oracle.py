@@ -436,3 +436,57 @@ def test_beam_cerny(n):
     assert R == (n - 1) ** 2 and resets(d, w)
     R1, w1, sizes = oracle.beam(d, 1)  # a beam of one still finds a word here
     assert R1 >= (n - 1) ** 2 and resets(d, w1) and max(sizes[1:] or [1]) == 1
+
+
+# ---------------------------------------------------------------- O5: the inverse DFS phase
+
+
+def _splits(r, span):
+    """Every split (i, j) with i + j <= r and at most `span` inverse steps left."""
+    return [(i, j) for i in range(r + 1) for j in range(r + 1 - i) if r - i - j <= span]
+
+
+def test_inverse_dfs_from_any_split_gives_r():
+    # Section 2.2: from the last levels F_i, B_j of any split below the
+    # meet, the inverse phase finds r exactly (O1's r; a phase that used
+    # images, tested Y inside X, or counted D off by one fails here)
+    rng = np.random.default_rng(55)
+    for t in range(30):
+        k = int(rng.choice([2, 3]))
+        n = int(rng.integers(3, 10))
+        d = gen.random_automaton(n, k, 900 + t)
+        r = oracle.forward(d)[0]
+        for i, j in _splits(r, 8 if k == 2 else 5):
+            assert oracle.inverse_dfs_r(d, i, j, max_depth=r) == r, (n, k, t, i, j)
+
+
+def test_inverse_dfs_cerny():
+    # r = (n - 1)^2 (Section 1.1) from splits up to ten inverse steps short
+    for n in range(3, 7):
+        d = gen.cerny(n)
+        r = (n - 1) ** 2
+        for i, j in _splits(r, 10):
+            assert oracle.inverse_dfs_r(d, i, j, max_depth=r) == r, (n, i, j)
+
+
+def test_inverse_dfs_every_binary_three_state_automaton():
+    import itertools
+    seen = 0
+    for a in itertools.product(range(3), repeat=3):
+        for b in itertools.product(range(3), repeat=3):
+            d = np.array([a, b], dtype=np.int32)
+            if not oracle.is_synchronizing(d):
+                continue
+            r = oracle.forward(d)[0]
+            for i, j in _splits(r, r):
+                assert oracle.inverse_dfs_r(d, i, j, max_depth=r) == r, (a, b, i, j)
+            seen += 1
+    assert seen > 100
+
+
+def test_inverse_dfs_not_found_below_the_needed_depth():
+    # the phase is exact: capped one step short of r it reports no meet
+    d = gen.cerny(5)
+    assert oracle.inverse_dfs_r(d, 3, 4, max_depth=16 - 7) == 16
+    with pytest.raises(oracle.OracleError):
+        oracle.inverse_dfs_r(d, 3, 4, max_depth=16 - 7 - 1)
