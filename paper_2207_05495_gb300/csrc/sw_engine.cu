@@ -1634,10 +1634,12 @@ struct Engine {
     // One iteration over the active instances.  The next iteration's steps
     // are planned, and for a plain search staged, on the host while this
     // iteration's meet kernel runs.  The words of the instances that meet
-    // finds are recovered at the start of the next iteration, ahead of its
-    // expansion (so the device goes from one meet to the next expansion
-    // without waiting for the host), and end with that iteration's level
-    // sizes; a step staged for an instance that met is dropped.
+    // finds are recovered at the start of the next iteration, in the same
+    // upload and ahead of its expansion (so between one meet and the next
+    // expansion the host only drops the met instances' steps and uploads),
+    // and end with that iteration's level sizes.  Instances sent to the
+    // inverse phase by the planning run it at the start of an iteration (or
+    // at once when no other instance is active).
     int iterate() {
         g_stats.iterations++;
         auto t_sel = std::chrono::steady_clock::now();
