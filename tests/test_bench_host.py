@@ -118,3 +118,30 @@ def test_schedules_agree_words_only_when_unique():
     # r or a level both computed that differ: never an agreement
     assert not bench.schedules_agree(a, (6,) + a[1:], False)
     assert not bench.schedules_agree(a, (5, a[1], [1, 2, 4], [4, 6]), False)
+
+
+def test_meet_roofline_averages_the_timed_steps():
+    base = dict(meet_launches=4, meet_lane_words=2)
+    stats = [dict(base, meet_ms=10.0, pairs=100, and_iters=1000, rows_transposed=50),
+             dict(base, meet_ms=20.0, pairs=300, and_iters=3000, rows_transposed=150)]
+    assert bench.meet_roofline(stats, 152) == (15.0, 200.0, 2000.0, 100.0, 4.0, 2)
+    # the direct test reports 0 lane words: counted as one
+    stats[-1]["meet_lane_words"] = 0
+    assert bench.meet_roofline(stats, 152)[5] == 1
+
+
+def test_mark_roofline_counts_the_bitmap_work():
+    stats = [dict(mark_ms=2.0, mark_steps=1e9, mark_rows=1e8, mark_pairs=5e12)]
+    m = bench.mark_roofline(stats, lw=2, W=3, peak=40.0)
+    ops = 1e9 * 64 * 2 + 1e8 * 2 * 3 * 25  # AND words per step, 25 ops per transposed 32-bit word
+    assert abs(m["achieved"] - ops / 2e-3 / 1e12) < 1e-9
+    assert abs(m["frac"] - m["achieved"] / 40.0) < 1e-12
+    assert m["pairs_per_step"] == 5e12
+    assert bench.mark_roofline([dict(mark_ms=0.0, mark_steps=0, mark_rows=0, mark_pairs=0)], 2, 3, 40.0) is None
+
+
+def test_hbm_line_is_bytes_over_event_time():
+    line = bench.hbm_line(10.0, 68e9, (6800.0, "measured"), "basis")
+    assert abs(line["achieved"] - 6800.0) < 1e-9 and abs(line["frac"] - 1.0) < 1e-12
+    assert line["peak_basis"] == "measured copy bandwidth" and line["traffic"] is None
+    assert bench.hbm_line(0.0, 1e9, (6800.0, "fallback"), "b")["achieved"] == 0.0
