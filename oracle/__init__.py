@@ -58,7 +58,7 @@ def _load():
         lib.oracle_reduced_level_sizes.argtypes = [ctypes.c_int, ctypes.c_int, p, ctypes.c_int, i32, i64, p]
         lib.oracle_bidir_reduced.argtypes = [ctypes.c_int, ctypes.c_int, p, i64, i32, i32, p, p, i32, p, p, p, p, i32]
         lib.oracle_beam.argtypes = [ctypes.c_int, ctypes.c_int, p, i64, i32, p, p, i32, p, i32, p]
-        lib.oracle_inverse_dfs_r.argtypes = [ctypes.c_int, ctypes.c_int, p, i32, i32, i32, i64, p]
+        lib.oracle_inverse_dfs_r.argtypes = [ctypes.c_int, ctypes.c_int, p, i32, i32, i32, i32, i64, p]
         lib.oracle_beam.restype = ctypes.c_int
         for f in (lib.oracle_brute, lib.oracle_forward, lib.oracle_level_sizes, lib.oracle_bidir,
                   lib.oracle_is_synchronizing, lib.oracle_reduced_level_sizes, lib.oracle_bidir_reduced):
@@ -182,13 +182,16 @@ def beam(delta, beam_size: int, max_depth: int = 1 << 16):
     return int(r[0]), w[: r[0]].tolist(), sizes[: nl[0]].tolist()
 
 
-def inverse_dfs_r(delta, fwd_depth: int, bwd_depth: int, max_depth: int = 24, max_sets: int = 50_000_000) -> int:
+def inverse_dfs_r(delta, fwd_depth: int, bwd_depth: int, dirs: int = 0, max_depth: int = 24,
+                  max_sets: int = 50_000_000) -> int:
     """O5: r from the BFS level at fwd_depth and the IBFS level at bwd_depth
     by the inverse DFS phase of Section 2.2 (depth-first over preimages, no
-    history, brute-force subset checks against the BFS level)."""
+    history, brute-force subset checks against the BFS level).  dirs: bit 0
+    reduces the BFS side, bit 1 the IBFS side (Alg. 1's inclusion
+    reductions, as bidir_reduced)."""
     d, n, k = _delta(delta)
     r = np.zeros(1, np.int32)
-    rc = _load().oracle_inverse_dfs_r(n, k, _ptr(d), fwd_depth, bwd_depth, max_depth, max_sets, _ptr(r))
+    rc = _load().oracle_inverse_dfs_r(n, k, _ptr(d), fwd_depth, bwd_depth, dirs, max_depth, max_sets, _ptr(r))
     if rc:
         raise OracleError(rc, "oracle_inverse_dfs_r")
     return int(r[0])

@@ -42,11 +42,12 @@
  *                          largest preimages of every depth (the cut-off
  *                          inverse BFS the paper cites).
  *   oracle_inverse_dfs_r   Section 2.2: r from the last levels F_i, B_j of a
- *                          bidirectional search by the inverse DFS phase (a
- *                          depth-first search over preimages from every set
- *                          of B_j, no history, each set reached checked
- *                          against F_i by brute force), deepened one step at
- *                          a time.
+ *                          bidirectional search (plain or with the
+ *                          reductions of Alg. 1 on either side) by the
+ *                          inverse DFS phase (a depth-first search over
+ *                          preimages from every set of B_j, no history,
+ *                          each set reached checked against F_i by brute
+ *                          force), deepened one step at a time.
  *   oracle_is_synchronizing  Section 2, first step: every pair of states can
  *                          be mapped to one state.
  *
@@ -913,6 +914,28 @@ static int level_at(int n, int k, const int32_t *delta, int dir, int depth, int6
     return rc;
 }
 
+/* The reduced level of one direction at depth `depth` (Alg. 1 with its
+ * inclusion reductions, as oracle_reduced_level_sizes counts it), left in
+ * *out. */
+static int reduced_level_at(int n, int k, const int32_t *delta, int dir, int depth, int64_t max_sets,
+                            level_t *out) {
+    int W = words_for(n);
+    level_t *lv = (level_t *)calloc((size_t)depth + 1, sizeof(level_t));
+    if (!lv) return OR_ENOMEM;
+    int rc = dir == 0 ? level_root_Q(&lv[0], n, W) : level_root_singletons(&lv[0], n, W);
+    int64_t stored = lv[0].count;
+    for (int d = 1; !rc && d <= depth; d++) {
+        rc = expand_reduced(n, k, delta, dir, &lv[d - 1], lv, d, &lv[d], max_sets - stored);
+        if (!rc) stored += lv[d].count;
+        if (!rc && stored > max_sets) rc = OR_ETOOBIG;
+    }
+    for (int d = 0; d < depth; d++) level_free(&lv[d]);
+    if (rc) level_free(&lv[depth]);
+    else *out = lv[depth];
+    free(lv);
+    return rc;
+}
+
 /* Some X of F lies inside Y (brute force over F: the query the paper's
  * static trie answers). */
 static int some_subset(const level_t *F, const uint64_t *Y, int n, int W) {
@@ -943,18 +966,24 @@ static int dfs_reaches(int n, int k, const int32_t *delta, const level_t *F, con
  * it reaches against F_i.  D is deepened one step at a time (D = 0, 1, ...,
  * D = 0 being the meet of F_i and B_j themselves); the first D at which some
  * set of B_j reaches, after exactly D inverse steps, a superset of a set of
- * F_i gives r = fwd_depth + bwd_depth + D.  Returns OR_ENOTFOUND when no D up
- * to max_depth does.
+ * F_i gives r = fwd_depth + bwd_depth + D.  dirs: bit 0 takes F_i from the
+ * BFS with the inclusion reductions of Alg. 1, bit 1 takes B_j from the
+ * reduced IBFS (otherwise duplicates and the equality history only).
+ * Returns OR_ENOTFOUND when no D up to max_depth does.
  */
-int oracle_inverse_dfs_r(int n, int k, const int32_t *delta, int32_t fwd_depth, int32_t bwd_depth,
+int oracle_inverse_dfs_r(int n, int k, const int32_t *delta, int32_t fwd_depth, int32_t bwd_depth, int32_t dirs,
                          int32_t max_depth, int64_t max_sets, int32_t *r_out) {
     int rc = check_automaton(n, k, delta);
     if (rc) return rc;
-    if (fwd_depth < 0 || bwd_depth < 0 || max_depth < 0 || !r_out || n > 1024) return OR_EINVAL;
+    if (fwd_depth < 0 || bwd_depth < 0 || dirs < 0 || dirs > 3 || max_depth < 0 || !r_out || n > 1024)
+        return OR_EINVAL;
     int W = words_for(n);
     level_t F = {0}, B = {0};
-    rc = level_at(n, k, delta, 0, fwd_depth, max_sets, &F);
-    if (!rc) rc = level_at(n, k, delta, 1, bwd_depth, max_sets, &B);
+    rc = (dirs & 1) ? reduced_level_at(n, k, delta, 0, fwd_depth, max_sets, &F)
+                    : level_at(n, k, delta, 0, fwd_depth, max_sets, &F);
+    if (!rc)
+        rc = (dirs & 2) ? reduced_level_at(n, k, delta, 1, bwd_depth, max_sets, &B)
+                        : level_at(n, k, delta, 1, bwd_depth, max_sets, &B);
     uint64_t *buf = rc ? NULL : (uint64_t *)malloc((size_t)(max_depth + 1) * W * sizeof(uint64_t));
     if (!rc && !buf) rc = OR_ENOMEM;
     int found = -1;

@@ -490,3 +490,19 @@ def test_inverse_dfs_not_found_below_the_needed_depth():
     assert oracle.inverse_dfs_r(d, 3, 4, max_depth=16 - 7) == 16
     with pytest.raises(oracle.OracleError):
         oracle.inverse_dfs_r(d, 3, 4, max_depth=16 - 7 - 1)
+
+
+def test_inverse_dfs_after_reduced_levels_gives_r():
+    # the phase may start from reduced levels (Alg. 1's inclusion reductions
+    # on either side): each kept level holds a subset (BFS) or superset
+    # (IBFS) of every set first reached at its depth, so from any split
+    # below the meet it still finds r
+    rng = np.random.default_rng(77)
+    for t in range(20):
+        k = int(rng.choice([2, 3]))
+        n = int(rng.integers(3, 9))
+        d = gen.random_automaton(n, k, 1300 + t)
+        r = oracle.forward(d)[0]
+        for dirs in (1, 2, 3):
+            for i, j in _splits(r, 7 if k == 2 else 4):
+                assert oracle.inverse_dfs_r(d, i, j, dirs=dirs, max_depth=r) == r, (n, k, t, dirs, i, j)
