@@ -353,7 +353,7 @@ def main():
     ap.add_argument("--no-serve", action="store_true")
     ap.add_argument("--opt", action="append", default=[],
                     help="override a search option after tuning, e.g. --opt meet_lane_words=4")
-    ap.add_argument("--serve-requests", type=int, default=1500)
+    ap.add_argument("--serve-requests", type=int, default=2000)
     ap.add_argument("--one-schedule", action="store_true",
                     help="hard workloads: skip the second (balanced) schedule")
     args = ap.parse_args()
