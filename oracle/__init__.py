@@ -59,6 +59,8 @@ def _load():
         lib.oracle_bidir_reduced.argtypes = [ctypes.c_int, ctypes.c_int, p, i64, i32, i32, p, p, i32, p, p, p, p, i32]
         lib.oracle_beam.argtypes = [ctypes.c_int, ctypes.c_int, p, i64, i32, p, p, i32, p, i32, p]
         lib.oracle_inverse_dfs_r.argtypes = [ctypes.c_int, ctypes.c_int, p, i32, i32, i32, i32, i64, p]
+        lib.oracle_mark_supersets.argtypes = [ctypes.c_int, p, i64, p, i64, ctypes.c_int, i32, p]
+        lib.oracle_mark_supersets.restype = i64
         lib.oracle_beam.restype = ctypes.c_int
         for f in (lib.oracle_brute, lib.oracle_forward, lib.oracle_level_sizes, lib.oracle_bidir,
                   lib.oracle_is_synchronizing, lib.oracle_reduced_level_sizes, lib.oracle_bidir_reduced):
@@ -195,6 +197,22 @@ def inverse_dfs_r(delta, fwd_depth: int, bwd_depth: int, dirs: int = 0, max_dept
     if rc:
         raise OracleError(rc, "oracle_inverse_dfs_r")
     return int(r[0])
+
+
+def mark_supersets(n: int, A, B, proper: bool = False, min_brute: int = 4):
+    """O6, Alg. 2: boolean marks of the sets of B (uint64 [nb][W] bitsets)
+    that contain (properly, when proper) some set of A (uint64 [na][W],
+    sorted lexicographically from state 0, absent before present, no
+    repeats)."""
+    W = (n + 63) // 64
+    A = np.ascontiguousarray(np.asarray(A, dtype=np.uint64).reshape(-1, W))
+    B = np.ascontiguousarray(np.asarray(B, dtype=np.uint64).reshape(-1, W))
+    marks = np.zeros(max(len(B), 1), np.uint8)
+    rc = _load().oracle_mark_supersets(n, _ptr(A), len(A), _ptr(B), len(B), int(bool(proper)), min_brute,
+                                       _ptr(marks))
+    if rc < 0:
+        raise OracleError(int(rc), "oracle_mark_supersets")
+    return marks[: len(B)].astype(bool)
 
 
 def is_synchronizing(delta) -> bool:

@@ -48,6 +48,11 @@
  *                          preimages from every set of B_j, no history,
  *                          each set reached checked against F_i by brute
  *                          force), deepened one step at a time.
+ *   oracle_mark_supersets  Alg. 2 (MarkSupersets / MarkProperSupersets,
+ *                          Section 2.1.1): the sets of B that contain some
+ *                          set of A, by recursive splitting of the sorted
+ *                          list A on one state per level, brute force on
+ *                          small intervals.
  *   oracle_is_synchronizing  Section 2, first step: every pair of states can
  *                          be mapped to one state.
  *
@@ -996,6 +1001,111 @@ int oracle_inverse_dfs_r(int n, int k, const int32_t *delta, int32_t fwd_depth, 
     level_free(&F);
     level_free(&B);
     return rc;
+}
+
+/* ------------------------------------------------------------------ */
+/* O6: MarkSupersets by recursive state splitting (Alg. 2, §2.1.1)     */
+/* ------------------------------------------------------------------ */
+
+/* The recursion of Alg. 2 on intervals: A[a0, a1) (indices into the sorted
+ * list A, all agreeing on states 0 .. d-1) and the live part bi[b0, b1) of
+ * B (indices not marked yet).  A marked B index is swapped to the end of
+ * the live part and the interval shrinks, so the live part of every caller
+ * stays a prefix of its interval. */
+typedef struct {
+    const uint64_t *A, *B;
+    int n, W, proper, min_brute;
+    int64_t *bi;     /* permutation of B's indices */
+    uint8_t *mark;   /* mark[b] = 1: B[b] is a (proper) superset of some set of A */
+} mark_ctx_t;
+
+static int64_t mark_rec(mark_ctx_t *c, int64_t a0, int64_t a1, int64_t b0, int64_t b1, int d) {
+    /* returns the new end of the live part b1 */
+    const int W = c->W;
+    if (a1 - a0 <= c->min_brute || d >= c->n) {
+        for (int64_t p = b0; p < b1;) {
+            const uint64_t *Y = c->B + c->bi[p] * W;
+            int hit = 0;
+            for (int64_t a = a0; a < a1 && !hit; a++) {
+                const uint64_t *X = c->A + a * W;
+                if (set_subset(X, Y, c->n) && !(c->proper && set_cmp(X, Y, c->n) == 0)) hit = 1;
+            }
+            if (hit) {
+                c->mark[c->bi[p]] = 1;
+                int64_t t = c->bi[p];
+                c->bi[p] = c->bi[b1 - 1];
+                c->bi[b1 - 1] = t;
+                b1--;
+            } else {
+                p++;
+            }
+        }
+        return b1;
+    }
+    /* A_0 (state d absent) comes first in the sorted interval: find the cut */
+    int64_t lo = a0, hi = a1;
+    while (lo < hi) {
+        int64_t mid = lo + (hi - lo) / 2;
+        if (set_has(c->A + mid * W, d)) hi = mid;
+        else lo = mid + 1;
+    }
+    const int64_t cut = lo;
+    /* A_0 may lie inside any live set of B */
+    if (cut > a0) b1 = mark_rec(c, a0, cut, b0, b1, d + 1);
+    if (cut < a1) {
+        /* a set of A_1 holds state d: only live B sets holding it qualify;
+         * order the live part so that they form its suffix */
+        int64_t p = b0, q = b1;
+        while (p < q) {
+            if (set_has(c->B + c->bi[p] * W, d)) {
+                q--;
+                int64_t t = c->bi[p];
+                c->bi[p] = c->bi[q];
+                c->bi[q] = t;
+            } else {
+                p++;
+            }
+        }
+        /* B_1 = bi[q, b1); marks inside it shrink it from its end, so the
+         * live part stays bi[b0, b1') with the marked indices after it */
+        int64_t e = mark_rec(c, cut, a1, q, b1, d + 1);
+        b1 = e;
+    }
+    return b1;
+}
+
+/*
+ * Alg. 2 (MarkSupersets, Section 2.1.1): marks every set of B that is a
+ * superset (proper = 1: a proper superset, MarkProperSupersets) of some set
+ * of A.  A: na sets sorted lexicographically (state 0 first, absent before
+ * present) with no repeats; B: nb sets in any order.  A lists of at most
+ * min_brute sets is checked against the live part of B pair by pair (the
+ * paper's MIN); otherwise A is split by the current state d and the two
+ * halves recurse, the half holding d only against the B sets that hold d.
+ * mark_out[b] = 1 for the marked sets of B.  Returns the number marked.
+ */
+int64_t oracle_mark_supersets(int n, const uint64_t *A, int64_t na, const uint64_t *B, int64_t nb, int proper,
+                              int32_t min_brute, uint8_t *mark_out) {
+    if (n < 1 || n > 4096 || na < 0 || nb < 0 || (na && !A) || (nb && !B) || !mark_out || min_brute < 1)
+        return OR_EINVAL;
+    const int W = words_for(n);
+    for (int64_t a = 1; a < na; a++)
+        if (set_cmp(A + (a - 1) * W, A + a * W, n) >= 0) return OR_EINVAL; /* not sorted and unique */
+    mark_ctx_t c;
+    c.A = A;
+    c.B = B;
+    c.n = n;
+    c.W = W;
+    c.proper = proper ? 1 : 0;
+    c.min_brute = min_brute;
+    c.bi = (int64_t *)malloc((size_t)(nb ? nb : 1) * sizeof(int64_t));
+    if (!c.bi) return OR_ENOMEM;
+    c.mark = mark_out;
+    memset(mark_out, 0, (size_t)nb);
+    for (int64_t b = 0; b < nb; b++) c.bi[b] = b;
+    int64_t live_end = na ? mark_rec(&c, 0, na, 0, nb, 0) : nb;
+    free(c.bi);
+    return nb - live_end;
 }
 
 /* ------------------------------------------------------------------ */

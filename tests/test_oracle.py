@@ -506,3 +506,78 @@ def test_inverse_dfs_after_reduced_levels_gives_r():
         for dirs in (1, 2, 3):
             for i, j in _splits(r, 7 if k == 2 else 4):
                 assert oracle.inverse_dfs_r(d, i, j, dirs=dirs, max_depth=r) == r, (n, k, t, dirs, i, j)
+
+
+# ---------------------------------------------------------------- O6: MarkSupersets (Alg. 2)
+
+
+def _random_sets(rng, n, m, density):
+    """m random subsets of {0..n-1} as uint64 [m][W] bitsets."""
+    W = (n + 63) // 64
+    bits = rng.random((m, n)) < density
+    out = np.zeros((m, W), np.uint64)
+    for q in range(n):
+        out[:, q // 64] |= bits[:, q].astype(np.uint64) << np.uint64(q % 64)
+    return out
+
+
+def _lex_sorted_unique(sets, n):
+    # lexicographic order of characteristic vectors from state 0 upwards,
+    # absent before present (the order Alg. 2 requires of A)
+    def key(row):
+        return tuple(int((int(row[q // 64]) >> (q % 64)) & 1) for q in range(n))
+    rows = {key(r): r for r in sets}
+    return np.array([rows[k] for k in sorted(rows)], dtype=np.uint64).reshape(-1, sets.shape[1])
+
+
+def _brute_marks(A, B, proper):
+    marks = np.zeros(len(B), bool)
+    for b, Y in enumerate(B):
+        for X in A:
+            if not np.any(X & ~Y) and not (proper and np.array_equal(X, Y)):
+                marks[b] = True
+                break
+    return marks
+
+
+@pytest.mark.parametrize("n", [1, 5, 13, 64, 70, 130])
+def test_mark_supersets_equals_brute_force(n):
+    rng = np.random.default_rng(n)
+    for trial in range(12):
+        dens_a, dens_b = rng.uniform(0.05, 0.6), rng.uniform(0.3, 0.95)
+        A = _lex_sorted_unique(_random_sets(rng, n, int(rng.integers(0, 80)), dens_a), n)
+        B = _random_sets(rng, n, int(rng.integers(0, 120)), dens_b)
+        if len(A) and len(B):
+            B[: len(B) // 4] = A[rng.integers(0, len(A), len(B) // 4)]  # some equal pairs
+        for proper in (False, True):
+            want = _brute_marks(A, B, proper)
+            for mb in (1, 2, 8, 1000):  # the brute-force cut-off changes nothing
+                got = oracle.mark_supersets(n, A, B, proper=proper, min_brute=mb)
+                assert (got == want).all(), (n, trial, proper, mb)
+
+
+def test_mark_subsets_by_complements():
+    # MarkSubsets (the IBFS side) is MarkSupersets on the complements
+    rng = np.random.default_rng(9)
+    n = 40
+    full = np.array([(1 << n) - 1], dtype=np.uint64)
+    A = _random_sets(rng, n, 60, 0.7)
+    B = _random_sets(rng, n, 90, 0.3)
+    Ac = _lex_sorted_unique(A ^ full, n)
+    got = oracle.mark_supersets(n, Ac, B ^ full)
+    want = np.array([any(not np.any(Y & ~X) for X in A) for Y in B])  # Y inside some X
+    assert (got == want).all()
+
+
+def test_mark_supersets_rejects_unsorted_lists():
+    n = 8
+    # {0} comes before {0, 1}: they first differ at state 1, absent first
+    ordered = np.array([[0b01], [0b11]], dtype=np.uint64)
+    B = np.array([[0b01], [0b10], [0b11]], dtype=np.uint64)
+    assert oracle.mark_supersets(n, ordered, B).tolist() == [True, False, True]
+    assert oracle.mark_supersets(n, ordered, B, proper=True).tolist() == [False, False, True]
+    with pytest.raises(oracle.OracleError):
+        oracle.mark_supersets(n, ordered[::-1].copy(), B)
+    with pytest.raises(oracle.OracleError):  # a repeat
+        oracle.mark_supersets(n, np.array([[0b01], [0b01]], dtype=np.uint64), B)
+    assert oracle.mark_supersets(n, np.zeros((0, 1), np.uint64), B).tolist() == [False, False, False]
